@@ -1,0 +1,389 @@
+"""Benchmark of the GB300 Game of Life library.
+
+Default workload (one "step"): the uneven batch of 4096 toroidal packed
+boards -- rows and cols log-uniform in [32, 2048] rounded to multiples of
+64, density U(0.1, 0.6), generations log-uniform in [100, 5000] -- advanced
+by one gol_step_batch call (one persistent launch).  The headline value is
+batched GCUPS (cell updates per second / 1e9); the same line carries the
+plain one-board-at-a-time loop measured on a sample of the batch, the
+end-to-end figure through host buffers, the roofline of the dominant
+kernel, the oracle's CPU throughput and the SM clocks seen while timing.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload batch|single|bytes]
+
+``--impl reference`` times the oracle (the plain serial CPU program of
+``oracle/``) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+INT_OPS_PER_WORD_GEN = 24          # 4 funnel shifts + 20 LOP3 per 64-cell word per generation
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "single", "bytes"])
+    ap.add_argument("--boards", type=int, default=4096)
+    ap.add_argument("--plain-sample", type=int, default=64, help="boards timed in the plain loop")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9], parts[4]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(specs, seconds: float, threads: int = 1):
+    """Times the oracle on boards taken evenly from ``specs`` for a bounded
+    number of generations; returns (GCUPS, cores, description)."""
+    import oracle
+
+    oracle.build()
+    pick = specs[:: max(1, len(specs) // 16)][:16]
+    done_cells = 0
+    t0 = time.perf_counter()
+    used = 0
+    for s in pick:
+        cells = synth.bernoulli_board(s.rows, s.cols, s.density, s.seed)
+        g = min(s.gens, 8)
+        t = time.perf_counter()
+        if threads == 1:
+            oracle.run(cells, g)
+        else:
+            oracle.run_rows_omp(cells, g, threads)
+        used += time.perf_counter() - t
+        done_cells += s.rows * s.cols * g
+        if time.perf_counter() - t0 > seconds:
+            break
+    return done_cells / used / 1e9, threads, "%d boards of the batch (every %dth), min(gens, 8) generations each" % (
+        len(pick), max(1, len(specs) // 16))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, rank, world, local):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1209_4408_gb300 as gol
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = gol.use_torch_allocator(local)
+    dinfo = gol.gol_device_info()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- workload -----------------------------------------------------------
+    if args.workload == "batch":
+        specs = synth.batch_specs(args.boards)
+        # weak scaling: each rank steps its own copy of the batch with its own seeds
+        if rank:
+            specs = [synth.BoardSpec(s.index, s.rows, s.cols, s.density, s.gens,
+                                     synth.derive_seed(s.seed, rank)) for s in specs]
+        workload = "batch of %d uneven toroidal packed boards (rows, cols log-uniform [32, 2048] " \
+                   "rounded to x64; density U(0.1,0.6); gens log-uniform [100, 5000])" % len(specs)
+    elif args.workload == "single":
+        specs = [synth.BoardSpec(0, 16384, 16384, 0.5, 10000, synth.SEED_SINGLE_16K)]
+        workload = "single 16384x16384 toroidal packed board, Bernoulli(0.5), 10000 generations"
+    else:
+        specs = [synth.BoardSpec(0, 256, 256, 0.3, 1000, synth.SEED_BYTES_256)]
+        workload = "single 256x256 toroidal byte-per-cell board, Bernoulli(0.3), 1000 generations"
+
+    total_cells_gens = sum(s.rows * s.cols * s.gens for s in specs)
+    total_words_gens = sum(s.rows * (s.cols // 64) * s.gens for s in specs)
+    layout = gol.GOL_LAYOUT_BYTES if args.workload == "bytes" else gol.GOL_LAYOUT_PACKED
+    pinned, views, boards = None, [], []
+    if layout == gol.GOL_LAYOUT_PACKED:
+        nwords = sum(s.rows * s.cols // 64 for s in specs)
+        pinned = torch.empty(nwords, dtype=torch.int64, pin_memory=True)
+        host = pinned.numpy().view(np.uint64)
+        off = 0
+        for s in specs:
+            n = s.rows * s.cols // 64
+            v = host[off:off + n].reshape(s.rows, s.cols // 64)
+            if s.density == 0.5:
+                synth.random_words(s.rows, s.cols // 64, s.seed, out=v)
+            else:
+                v[:] = synth.bernoulli_words(s.rows, s.cols, s.density, s.seed)
+            views.append(v)
+            off += n
+            b = gol.Board(s.rows, s.cols, torus=True, layout=layout)
+            b.set_packed(v)
+            boards.append(b)
+    else:
+        for s in specs:
+            b = gol.Board(s.rows, s.cols, torus=True, layout=layout)
+            b.set(synth.bernoulli_board(s.rows, s.cols, s.density, s.seed))
+            boards.append(b)
+    handles = [b.handle for b in boards]
+    gens = [s.gens for s in specs]
+    torch.cuda.synchronize()
+
+    def step():
+        gol.gol_step_batch(handles, gens)
+
+    # ---- device-resident timing ------------------------------------------------
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        t_end.record(stream)
+        barrier()
+    clocks = clk.summary()
+    ms_total = t_start.elapsed_time(t_end)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = ms_total / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = total_cells_gens * world / (ms * 1e-3) / 1e9
+
+    # ---- plain loop: the same boards stepped one at a time -----------------------
+    plain = None
+    if args.workload == "batch" and args.plain_sample > 0:
+        idx = list(range(0, len(specs), max(1, len(specs) // args.plain_sample)))[:args.plain_sample]
+        cg = sum(specs[i].rows * specs[i].cols * specs[i].gens for i in idx)
+        for i in idx[:4]:
+            gol.gol_step(handles[i], specs[i].gens)        # warm-up: plans for single boards
+        torch.cuda.synchronize()
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in idx:
+            gol.gol_step(handles[i], specs[i].gens)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b_)
+        plain = {"value": cg / (pms * 1e-3) / 1e9, "unit": "GCUPS", "boards": len(idx),
+                 "sample": "every %dth board of the batch, each stepped alone with gol_step" %
+                           max(1, len(specs) // args.plain_sample)}
+
+    # ---- end to end through host buffers -------------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = max(1, min(args.steps, 3))
+        out_pinned = torch.empty_like(pinned) if pinned is not None else None
+        outs = []
+        if out_pinned is not None:
+            host_out = out_pinned.numpy().view(np.uint64)
+            off = 0
+            for s in specs:
+                n = s.rows * s.cols // 64
+                outs.append(host_out[off:off + n].reshape(s.rows, s.cols // 64))
+                off += n
+        barrier()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for _ in range(e2e_steps):
+            if layout == gol.GOL_LAYOUT_PACKED:
+                for b, v in zip(boards, views):
+                    gol.gol_set_packed(b.handle, v)
+                    h2d += v.nbytes
+                step()
+                for b, o in zip(boards, outs):
+                    gol.gol_get_packed(b.handle, o)
+                    d2h += o.nbytes
+            else:
+                cells = [synth.bernoulli_board(s.rows, s.cols, s.density, s.seed) for s in specs]
+                for b, c in zip(boards, cells):
+                    b.set(c)
+                    h2d += c.nbytes
+                step()
+                for b in boards:
+                    d2h += b.get().nbytes
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": total_cells_gens * world / e2e_s / 1e9, "unit": "GCUPS",
+               "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps}
+
+    # ---- roofline of the dominant kernel (the persistent step kernel) ---------------
+    ops, _ = gol.gol_probe_int_throughput()
+    achieved_tops = total_words_gens * INT_OPS_PER_WORD_GEN / (min(step_ms) * 1e-3) / 1e12 \
+        if layout == gol.GOL_LAYOUT_PACKED else None
+    roofline = None
+    if achieved_tops is not None:
+        peak = ops / 1e12
+        roofline = {"bound": "alu", "achieved": round(achieved_tops, 3), "peak": round(peak, 3),
+                    "unit": "Tops/s", "frac": round(achieved_tops / peak, 4), "traffic": None,
+                    "peak_source": "integer-pipe probe (LOP3/funnel-shift mix) measured in this run",
+                    "algorithmic_ops_per_launch": total_words_gens * INT_OPS_PER_WORD_GEN}
+
+    out = {
+        "metric": "GCUPS batched (gol_step_batch) vs plain per-board loop on 1 GB300",
+        "value": round(value, 2), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64" if layout == gol.GOL_LAYOUT_PACKED else "u8",
+        "data": "synthetic (seeded SplitMix64 Bernoulli boards)",
+        "config": {"workload": workload, "boards": len(specs), "cell_updates_per_step": total_cells_gens,
+                   "l2": "working set (2 buffers per board) larger than L2" if total_cells_gens and
+                   sum(s.rows * s.cols // 4 for s in specs) > dinfo["l2_bytes"] else "fits in L2",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "clocks": clocks,
+        "gpu_launches": 2 * args.steps,
+        "step_ms": [round(x, 3) for x in step_ms],
+    }
+    if plain:
+        out["plain_loop"] = plain
+        out["speedup_vs_plain"] = round(value / world / plain["value"], 2)
+    if e2e:
+        out["e2e"] = e2e
+    if roofline:
+        out["roofline"] = roofline
+    if rank == 0:
+        g, cores, desc = cpu_oracle_sample(specs, args.cpu_seconds, 1)
+        out["cpu_baseline"] = {"value": round(g, 5), "unit": "GCUPS", "cores": cores, "kind": "oracle",
+                               "sample": desc}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores: each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    specs = synth.batch_specs(args.boards) if args.workload == "batch" else \
+        [synth.BoardSpec(0, 256, 256, 0.3, 1000, synth.SEED_BYTES_256)]
+    pick = specs[:: max(1, len(specs) // 8)][:8]
+    boards = [(s, synth.bernoulli_board(s.rows, s.cols, s.density, s.seed)) for s in pick]
+    gens = 2
+
+    def step():
+        n = 0
+        for s, c in boards:
+            oracle.run(c, gens)
+            n += s.rows * s.cols * gens
+        return n
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.steps):
+        n += step()
+    dt = time.perf_counter() - t0
+    v = n / dt / 1e9
+    desc = "%d boards taken evenly from the batch, %d generations each per step" % (len(pick), gens)
+    out = {"impl": "reference", "metric": "GCUPS batched (gol_step_batch) vs plain per-board loop on 1 GB300",
+           "value": round(v, 6), "unit": "GCUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded SplitMix64 Bernoulli boards)",
+           "config": {"workload": "oracle (serial, one byte per cell) on a bounded sample of the batch"},
+           "cpu_baseline": {"value": round(v, 6), "unit": "GCUPS", "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": round(v, 6), "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

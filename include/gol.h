@@ -1,0 +1,179 @@
+/*
+ * gol.h -- C ABI of the GB300 Game of Life library (libgol.so).
+ *
+ * The operation is the generation step of Section 1 of "A performance
+ * Analysis of the Game of Life based on parallel algorithm" (Ma, Chen,
+ * Meng): every cell counts its eight horizontally, vertically and
+ * diagonally adjacent neighbours and the four transitions of Section 1
+ * are applied to all cells at once.  The board's left and right edges and
+ * its top and bottom edges are adjacent (Section 2.2), i.e. the board is a
+ * torus; a bounded board whose outside cells are dead is also offered
+ * (torus = 0).
+ *
+ * Conventions shared by every call:
+ *   - cells are uint8 0/1, row major, `rows` rows of `cols` columns;
+ *   - the packed layout is uint64 words, row major, cols/64 words per row,
+ *     bit j of word k of a row holding column 64*k + j;
+ *   - host pointers belong to the caller and are not kept after the call
+ *     returns; device state belongs to the handle;
+ *   - every call returns GOL_OK (0) or a negative error code, and a
+ *     message for the calling thread is available from gol_last_error();
+ *   - stepping is asynchronous on the library's current CUDA stream
+ *     (gol_set_stream); calls that return data to the host synchronise it.
+ *
+ * The library needs a CUDA GPU; there is no CPU path.  Calls made without
+ * one return GOL_ECUDA.
+ */
+#ifndef GOL_H
+#define GOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GOL_OK 0
+#define GOL_EINVAL (-1)   /* bad argument: null pointer, size mismatch, cell value not 0/1 ... */
+#define GOL_ENOMEM (-2)   /* device allocation failed (including the allocator hook)          */
+#define GOL_ECUDA (-3)    /* a CUDA call failed (no device, launch error ...)                  */
+#define GOL_ETIMEOUT (-4) /* a bounded device-side wait gave up; the result is not valid       */
+#define GOL_EBUSY (-5)    /* the handle is in use by an unfinished batch                          */
+
+/* Board storage chosen at creation. */
+#define GOL_LAYOUT_AUTO 0   /* packed when cols % 64 == 0, else bytes                           */
+#define GOL_LAYOUT_PACKED 1 /* 64 cells per uint64 (cols % 64 == 0 required)                     */
+#define GOL_LAYOUT_BYTES 2  /* one uint8 per cell, any rows, cols >= 1                            */
+
+typedef struct gol_board *gol_handle;
+
+/* Creates a board of `rows` x `cols` dead cells (rows, cols >= 1) with the
+ * wrap-around edges of Section 2.2 when torus != 0, dead outside otherwise.
+ * Layout GOL_LAYOUT_AUTO.  Two device buffers of the board's size are
+ * allocated (through the allocator hook if one is set).  Errors: GOL_EINVAL
+ * for sizes < 1 or a null `out`, GOL_ENOMEM, GOL_ECUDA. */
+int gol_create(int64_t rows, int64_t cols, int torus, gol_handle *out);
+
+/* As gol_create with an explicit layout (GOL_LAYOUT_*).  GOL_LAYOUT_PACKED
+ * with cols % 64 != 0 is GOL_EINVAL. */
+int gol_create_ex(int64_t rows, int64_t cols, int torus, int layout, gol_handle *out);
+
+/* Frees the board's device memory after its stream's work has finished.
+ * A null handle is GOL_EINVAL. */
+int gol_destroy(gol_handle h);
+
+/* Initial configuration (Section 1: "creating an initial configuration").
+ * `cells` is host memory, rows*cols bytes, each 0 or 1; n must equal
+ * rows*cols.  Any other value is GOL_EINVAL and leaves the board as it was.
+ * Resets the generation counter to 0.  Synchronous. */
+int gol_set(gol_handle h, const uint8_t *cells, size_t n);
+
+/* Copies the current state to host `cells` (n == rows*cols bytes, 0/1).
+ * Synchronises the stream first. */
+int gol_get(gol_handle h, uint8_t *cells, size_t n);
+
+/* Packed variants: `words` is host memory of nwords == rows*cols/64 words
+ * in the packed layout.  Only for packed boards (else GOL_EINVAL).
+ * gol_set_packed resets the generation counter. */
+int gol_set_packed(gol_handle h, const uint64_t *words, size_t nwords);
+int gol_get_packed(gol_handle h, uint64_t *words, size_t nwords);
+
+/* Device-to-device variants for callers that keep boards on the GPU:
+ * `dwords` is device memory (nwords words, packed layout), read or written
+ * on the library's current stream; asynchronous. */
+int gol_set_packed_device(gol_handle h, const uint64_t *dwords, size_t nwords);
+int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords);
+
+/* Copies the nr x nc window whose top-left cell is (r0, c0) to host `out`
+ * (nr*nc bytes, row major).  Window indices are taken modulo the board
+ * size, so windows may straddle the wrap.  nr, nc >= 0. */
+int gol_get_region(gol_handle h, int64_t r0, int64_t c0, int64_t nr, int64_t nc, uint8_t *out);
+
+/* Advances the board by `generations` >= 0 steps (0 is a no-op).
+ * Asynchronous; the result is bit-identical to applying the step of
+ * Section 1 `generations` times.  Packed boards run several generations
+ * per pass over the board (temporal blocking).  Returns GOL_ETIMEOUT if a
+ * device-side wait gave up (the board is then in an unspecified state). */
+int gol_step(gol_handle h, int64_t generations);
+
+/* Advances handle hs[i] by generations[i] steps for i < n, all boards in
+ * one persistent device launch (packed boards; byte boards are stepped
+ * one by one).  Each board's result is bit-identical to gol_step on that
+ * board alone.  Handles must be distinct (else GOL_EINVAL).  A repeated
+ * call with the same handles and generation counts replays a captured CUDA
+ * graph.  Asynchronous; errors as gol_step. */
+int gol_step_batch(const gol_handle *hs, const int64_t *generations, size_t n);
+
+/* Number of live cells (the quantity of the paper's Table 1).
+ * Synchronous. */
+int gol_population(gol_handle h, uint64_t *out);
+
+/* Generations applied since the last gol_set / gol_set_packed. */
+int gol_generation(gol_handle h, int64_t *out);
+
+/* Board geometry: rows, cols, torus flag and layout (GOL_LAYOUT_PACKED or
+ * GOL_LAYOUT_BYTES). Any output pointer may be null. */
+int gol_info(gol_handle h, int64_t *rows, int64_t *cols, int *torus, int *layout);
+
+/* Waits for the library's current stream and reports any device-side
+ * error recorded by earlier asynchronous calls on this handle. */
+int gol_sync(gol_handle h);
+
+/* Sets the CUDA stream (a cudaStream_t, e.g. a torch stream's handle) on
+ * which subsequent calls of the calling process run; null selects the
+ * default stream. */
+int gol_set_stream(void *cuda_stream);
+
+/* Routes device allocations through alloc(size, ctx) / free(ptr, ctx)
+ * (e.g. the PyTorch caching allocator).  Passing two nulls restores
+ * cudaMalloc / cudaFree.  Boards keep the allocator they were made with. */
+int gol_set_allocator(void *(*alloc_fn)(size_t, void *), void (*free_fn)(void *, void *), void *ctx);
+
+/* Message for the last error of the calling thread ("" if none). */
+const char *gol_last_error(void);
+
+/* Tuning knobs (process wide).  Keys:
+ *   GOL_OPT_GENS_PER_PASS  generations per pass over a packed board (1, 2,
+ *                          4, 8 or 16; 0 = let the autotune table decide)
+ *   GOL_OPT_TILE_ROWS      rows per warp strip of a packed board (>= 1;
+ *                          0 = autotune table)
+ *   GOL_OPT_USE_GRAPHS     1 = capture/replay gol_step_batch in CUDA graphs
+ *   GOL_OPT_WAIT_TIMEOUT_MS  limit of the device-side bounded waits
+ *                          (default 5000 ms without progress)
+ * Unknown keys or values are GOL_EINVAL. */
+#define GOL_OPT_GENS_PER_PASS 1
+#define GOL_OPT_TILE_ROWS 2
+#define GOL_OPT_USE_GRAPHS 3
+#define GOL_OPT_WAIT_TIMEOUT_MS 4
+int gol_set_option(int key, int64_t value);
+int gol_get_option(int key, int64_t *value);
+
+/* Autotune table: the (generations per pass, tile rows) pair used for
+ * packed boards of a size class.  Size classes are keyed by
+ * (ceil(log2(rows)), words per row class); gol_tune_set fixes the entry for
+ * the class of (rows, cols), gol_tune_get reads the entry that would be
+ * used. */
+int gol_tune_set(int64_t rows, int64_t cols, int gens_per_pass, int tile_rows);
+int gol_tune_get(int64_t rows, int64_t cols, int *gens_per_pass, int *tile_rows);
+
+/* Device facts used for rooflines: SM count, L2 bytes, SM clock (kHz). */
+int gol_device_info(int *sm_count, int64_t *l2_bytes, int *sm_clock_khz);
+
+/* Integer-pipe throughput probe: runs a kernel of independent 32-bit
+ * LOP3/funnel-shift chains in the step's instruction mix on every SM and
+ * returns operations per second in *ops_per_s and the kernel time. */
+int gol_probe_int_throughput(double *ops_per_s, double *seconds);
+
+/* Test hook for the bounded device-side waits: launches the batch
+ * scheduler with one more work ticket than there is work, so that one
+ * waiter waits for a slot that nothing fills; with a timeout of
+ * `timeout_ms` it must give up and the call must return GOL_ETIMEOUT while
+ * the context stays usable. */
+int gol_debug_unfilled_wait(int64_t timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GOL_H */

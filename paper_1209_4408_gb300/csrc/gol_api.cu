@@ -1,0 +1,926 @@
+// C ABI of libgol: handles, host<->device transfers, planning of packed
+// steps into units, the plan/graph cache and the autotune table.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <set>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+#include "gol_internal.h"
+
+using namespace gol;
+
+struct gol_board {
+    int64_t rows = 0, cols = 0, words = 0;   // words per row (packed)
+    int torus = 1;
+    int layout = GOL_LAYOUT_PACKED;
+    void *buf[2] = {nullptr, nullptr};
+    int32_t *dev_cur = nullptr;              // device copy of `cur`
+    int cur = 0;                             // host mirror
+    int64_t generation = 0;
+    size_t buf_bytes = 0;
+    void *(*alloc_fn)(size_t, void *) = nullptr;
+    void (*free_fn)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+    uint64_t serial = 0;                     // identity for the plan cache
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+thread_local std::string t_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(GOL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(expr)                                              \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #expr);   \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// process state
+// ---------------------------------------------------------------------------
+std::mutex g_mu;
+cudaStream_t g_stream = nullptr;
+void *(*g_alloc)(size_t, void *) = nullptr;
+void (*g_free)(void *, void *) = nullptr;
+void *g_alloc_ctx = nullptr;
+int64_t g_opt_k = 0, g_opt_rows = 0, g_opt_graphs = 1, g_opt_timeout_ms = 5000;
+uint64_t g_serial = 0;
+
+struct DeviceState {
+    bool ready = false;
+    int device = -1;
+    int sms = 0;
+    int64_t l2 = 0;
+    int clock_khz = 0;
+    int32_t *sticky = nullptr;   // process-wide device error word
+};
+DeviceState g_dev;
+
+int ensure_device() {
+    if (g_dev.ready) return GOL_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice (no CUDA device?)");
+    cudaDeviceProp p;
+    CU(cudaGetDeviceProperties(&p, dev));
+    g_dev.device = dev;
+    g_dev.sms = p.multiProcessorCount;
+    g_dev.l2 = p.l2CacheSize;
+    int clk = 0;
+    cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev);
+    g_dev.clock_khz = clk;
+    CU(cudaMalloc(&g_dev.sticky, sizeof(int32_t)));
+    CU(cudaMemset(g_dev.sticky, 0, sizeof(int32_t)));
+    g_dev.ready = true;
+    return GOL_OK;
+}
+
+// allocation through the hook of the caller (board) or the process
+void *dev_alloc(size_t n, void *(*af)(size_t, void *), void *ctx) {
+    if (n == 0) n = 1;
+    if (af) return af(n, ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, n) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+void dev_free(void *p, void (*ff)(void *, void *), void *ctx) {
+    if (!p) return;
+    if (ff)
+        ff(p, ctx);
+    else
+        cudaFree(p);
+}
+
+// scoped temporary device buffer using the process allocator
+struct Scratch {
+    void *p = nullptr;
+    void *(*af)(size_t, void *) = g_alloc;
+    void (*ff)(void *, void *) = g_free;
+    void *ctx = g_alloc_ctx;
+    explicit Scratch(size_t n) { p = dev_alloc(n, af, ctx); }
+    ~Scratch() {
+        if (p) {
+            if (!ff) cudaStreamSynchronize(g_stream);
+            dev_free(p, ff, ctx);
+        }
+    }
+};
+
+// read and clear the sticky device error
+int take_sticky() {
+    if (!g_dev.ready) return GOL_OK;
+    int32_t v = 0;
+    cudaError_t e = cudaMemcpy(&v, g_dev.sticky, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading device status");
+    if (v != 0) {
+        int32_t z = 0;
+        cudaMemcpy(g_dev.sticky, &z, sizeof z, cudaMemcpyHostToDevice);
+        return fail(v, "a device-side bounded wait gave up (status %d); results are not valid", v);
+    }
+    return GOL_OK;
+}
+
+int sync_stream() {
+    CU(cudaStreamSynchronize(g_stream));
+    return take_sticky();
+}
+
+bool valid(gol_handle h) { return h != nullptr && h->rows > 0; }
+
+// ---------------------------------------------------------------------------
+// autotune table
+// ---------------------------------------------------------------------------
+struct TuneEntry {
+    int k;
+    int rows;
+};
+std::map<std::pair<int, int>, TuneEntry> g_tune;
+
+int ilog2_ceil(int64_t x) {
+    int l = 0;
+    while ((int64_t(1) << l) < x) ++l;
+    return l;
+}
+std::pair<int, int> size_class(int64_t rows, int64_t cols) {
+    const int64_t w = (cols + 63) / 64;
+    const int wc = w <= 32 ? (int)w : 32 + ilog2_ceil(w);
+    return {ilog2_ceil(rows), wc};
+}
+TuneEntry tune_lookup(int64_t rows, int64_t cols) {
+    auto it = g_tune.find(size_class(rows, cols));
+    TuneEntry t{8, 64};
+    if (it != g_tune.end()) t = it->second;
+    if (g_opt_k) t.k = (int)g_opt_k;
+    if (g_opt_rows) t.rows = (int)g_opt_rows;
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------
+struct Plan {
+    std::vector<gol_handle> hs;
+    std::vector<int64_t> gens;
+    std::vector<uint64_t> serials;
+    int K = 8;
+    bool torus = true;
+    int64_t opt_k = 0, opt_rows = 0;
+    // host copies
+    std::vector<BoardDesc> boards;
+    std::vector<UnitDesc> units;
+    std::vector<int32_t> npass;      // per board
+    int64_t total_tasks = 0;
+    // device memory
+    void *dmem = nullptr;
+    size_t dbytes = 0;
+    PersistArgs args{};
+    int grid = 1;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    uint64_t uses = 0;
+    void (*free_fn)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+    ~Plan() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (dmem) dev_free(dmem, free_fn, alloc_ctx);
+    }
+};
+
+int supported_k(int k) {
+    int s = 1;
+    while (s * 2 <= k && s < 16) s *= 2;
+    return s;
+}
+
+// split rows [0, R) into nb balanced blocks; block i = [R*i/nb, R*(i+1)/nb)
+void build_units(const gol_board *h, int bindex, int K, int tile_rows, std::vector<UnitDesc> &units,
+                 int32_t *nunits_out) {
+    const int R = (int)h->rows, W = (int)h->words;
+    const bool full = W <= 32;
+    const int S = full ? std::max(1, 32 / W) : 1;
+    const int nt = full ? 1 : (W + kTileWords - 1) / kTileWords;
+    // rows per unit: S segments of tile_rows rows (FULL) or tile_rows (TILED)
+    int64_t target = (int64_t)S * std::max(1, tile_rows);
+    int nb = (int)std::max<int64_t>(1, (R + target - 1) / target);
+    // with more than one block every block must be >= K rows so that a halo
+    // reaches only the adjacent blocks
+    if (nb > 1 && R / nb < K) nb = std::max(1, R / K);
+    const int first = (int)units.size();
+    for (int i = 0; i < nb; ++i) {
+        const int r0 = (int)((int64_t)R * i / nb), r1 = (int)((int64_t)R * (i + 1) / nb);
+        const int bh = r1 - r0;
+        for (int t = 0; t < nt; ++t) {
+            UnitDesc u{};
+            u.board = bindex;
+            u.r0 = r0;
+            u.r_end = r1;
+            if (full) {
+                u.mode = kUnitFull;
+                u.H = (bh + S - 1) / S;
+                u.S = (bh + u.H - 1) / u.H;
+                u.w0 = 0;
+                u.U = W;
+            } else {
+                u.mode = kUnitTiled;
+                u.H = bh;
+                u.S = 1;
+                u.w0 = (int)((int64_t)W * t / nt);
+                u.U = (int)((int64_t)W * (t + 1) / nt) - u.w0;
+            }
+            u.nnb = 0;
+            units.push_back(u);
+        }
+    }
+    // neighbours: adjacent row blocks x adjacent tiles (wrapping), minus self
+    for (int i = 0; i < nb; ++i)
+        for (int t = 0; t < nt; ++t) {
+            UnitDesc &u = units[first + i * nt + t];
+            std::set<int> nbs;
+            const int di[3] = {-1, 0, 1};
+            for (int a : di)
+                for (int b : di) {
+                    const int ii = ((i + a) % nb + nb) % nb, tt = ((t + b) % nt + nt) % nt;
+                    const int id = first + ii * nt + tt;
+                    if (id != first + i * nt + t) nbs.insert(id);
+                }
+            for (int id : nbs) u.nb[u.nnb++] = id;
+        }
+    *nunits_out = nb * nt;
+}
+
+int build_plan(Plan &P) {
+    const size_t n = P.hs.size();
+    P.boards.clear();
+    P.units.clear();
+    P.npass.clear();
+    // one K per launch: the tuned K of the board with the most work
+    int64_t best_work = -1;
+    int K = 8;
+    for (size_t i = 0; i < n; ++i) {
+        const int64_t work = P.hs[i]->rows * P.hs[i]->cols * P.gens[i];
+        if (work > best_work) {
+            best_work = work;
+            K = tune_lookup(P.hs[i]->rows, P.hs[i]->cols).k;
+        }
+    }
+    P.K = supported_k(std::max(1, K));
+    P.total_tasks = 0;
+    for (size_t i = 0; i < n; ++i) {
+        gol_board *h = P.hs[i];
+        BoardDesc bd{};
+        bd.buf[0] = (uint64_t *)h->buf[0];
+        bd.buf[1] = (uint64_t *)h->buf[1];
+        bd.cur = h->dev_cur;
+        bd.R = (int32_t)h->rows;
+        bd.W = (int32_t)h->words;
+        bd.gens = (int32_t)P.gens[i];
+        bd.npass = (int32_t)((P.gens[i] + P.K - 1) / P.K);
+        const TuneEntry te = tune_lookup(h->rows, h->cols);
+        build_units(h, (int)i, P.K, te.rows, P.units, &bd.nunits);
+        P.total_tasks += (int64_t)bd.nunits * bd.npass;
+        P.boards.push_back(bd);
+        P.npass.push_back(bd.npass);
+    }
+    if (P.total_tasks >= (int64_t(1) << 31) || P.units.size() >= (size_t(1) << 30))
+        return fail(GOL_EINVAL, "batch too large for one launch (%lld tasks)", (long long)P.total_tasks);
+    // device memory: boards | units | done | claimed | ctr | ring
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t nb = P.boards.size(), nu = P.units.size();
+    const size_t o_units = al(nb * sizeof(BoardDesc));
+    const size_t o_done = o_units + al(nu * sizeof(UnitDesc));
+    const size_t o_claimed = o_done + al(nu * 4);
+    const size_t o_ctr = o_claimed + al(nu * 4);
+    const size_t o_ring = o_ctr + al((4 + nb) * 4);
+    P.dbytes = o_ring + al((size_t)P.total_tasks * 4);
+    P.dmem = dev_alloc(P.dbytes, g_alloc, g_alloc_ctx);
+    P.free_fn = g_free;
+    P.alloc_ctx = g_alloc_ctx;
+    if (!P.dmem) return fail(GOL_ENOMEM, "plan workspace of %zu bytes", P.dbytes);
+    char *base = (char *)P.dmem;
+    CU(cudaMemcpyAsync(base, P.boards.data(), nb * sizeof(BoardDesc), cudaMemcpyHostToDevice, g_stream));
+    CU(cudaMemcpyAsync(base + o_units, P.units.data(), nu * sizeof(UnitDesc), cudaMemcpyHostToDevice,
+                       g_stream));
+    PersistArgs &a = P.args;
+    a.boards = (const BoardDesc *)base;
+    a.units = (const UnitDesc *)(base + o_units);
+    a.done = (int32_t *)(base + o_done);
+    a.claimed = (int32_t *)(base + o_claimed);
+    a.ctr = (int32_t *)(base + o_ctr);
+    a.ring = (int32_t *)(base + o_ring);
+    a.sticky = g_dev.sticky;
+    a.nunits = (int32_t)nu;
+    a.total_tasks = (int32_t)P.total_tasks;
+    a.timeout_ns = g_opt_timeout_ms * 1000000ll;
+    int bps = 1;
+    cudaError_t e = cudaSuccess;
+    switch (P.K) {
+        case 1: e = persistent_occupancy<1>(P.torus, &bps); break;
+        case 2: e = persistent_occupancy<2>(P.torus, &bps); break;
+        case 4: e = persistent_occupancy<4>(P.torus, &bps); break;
+        case 8: e = persistent_occupancy<8>(P.torus, &bps); break;
+        default: e = persistent_occupancy<16>(P.torus, &bps); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    const int64_t max_blocks = (int64_t)g_dev.sms * std::max(1, bps);
+    const int64_t want = (int64_t)(nu + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    P.grid = (int)std::max<int64_t>(1, std::min(max_blocks, want));
+    return GOL_OK;
+}
+
+cudaError_t launch_plan_kernels(const Plan &P, cudaStream_t s) {
+    cudaError_t e = launch_sched_init(P.args, (int)P.boards.size(), s);
+    if (e != cudaSuccess) return e;
+    switch (P.K) {
+        case 1: return launch_persistent<1>(P.args, P.torus, P.grid, s);
+        case 2: return launch_persistent<2>(P.args, P.torus, P.grid, s);
+        case 4: return launch_persistent<4>(P.args, P.torus, P.grid, s);
+        case 8: return launch_persistent<8>(P.args, P.torus, P.grid, s);
+        default: return launch_persistent<16>(P.args, P.torus, P.grid, s);
+    }
+}
+
+// plan cache (most recently used first); evicted plans wait in the
+// graveyard until the work queued before their eviction has finished
+std::vector<std::unique_ptr<Plan>> g_plans;
+constexpr size_t kMaxPlans = 16;
+struct Grave {
+    std::unique_ptr<Plan> plan;
+    cudaEvent_t ev;
+};
+std::vector<Grave> g_graves;
+
+void bury(std::unique_ptr<Plan> p) {
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev, g_stream) != cudaSuccess) {
+        cudaGetLastError();
+        if (ev) cudaEventDestroy(ev);
+        cudaDeviceSynchronize();
+        return;   // plan freed now, after the device went idle
+    }
+    g_graves.push_back(Grave{std::move(p), ev});
+}
+
+void reap(bool all) {
+    for (size_t i = 0; i < g_graves.size();) {
+        if (all) cudaEventSynchronize(g_graves[i].ev);
+        if (cudaEventQuery(g_graves[i].ev) == cudaSuccess) {
+            cudaEventDestroy(g_graves[i].ev);
+            g_graves.erase(g_graves.begin() + i);
+        } else {
+            cudaGetLastError();
+            ++i;
+        }
+    }
+}
+
+void clear_plans() {
+    for (auto &p : g_plans) bury(std::move(p));
+    g_plans.clear();
+    reap(true);
+}
+
+Plan *find_plan(const std::vector<gol_handle> &hs, const std::vector<int64_t> &gens, bool torus) {
+    for (size_t i = 0; i < g_plans.size(); ++i) {
+        Plan &P = *g_plans[i];
+        if (P.torus != torus || P.hs.size() != hs.size() || P.opt_k != g_opt_k || P.opt_rows != g_opt_rows)
+            continue;
+        if (P.gens != gens || P.hs != hs) continue;
+        bool same = true;
+        for (size_t j = 0; j < hs.size() && same; ++j) same = P.serials[j] == hs[j]->serial;
+        if (!same) continue;
+        if (P.args.timeout_ns != g_opt_timeout_ms * 1000000ll) continue;
+        if (i) std::rotate(g_plans.begin(), g_plans.begin() + i, g_plans.begin() + i + 1);
+        return g_plans[0].get();
+    }
+    return nullptr;
+}
+
+void drop_plans_of(gol_handle h) {
+    for (size_t i = 0; i < g_plans.size();) {
+        if (std::find(g_plans[i]->hs.begin(), g_plans[i]->hs.end(), h) != g_plans[i]->hs.end()) {
+            bury(std::move(g_plans[i]));
+            g_plans.erase(g_plans.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+// run packed boards (all with the same torus flag) in one persistent launch
+int run_packed(const std::vector<gol_handle> &hs, const std::vector<int64_t> &gens, bool torus) {
+    if (hs.empty()) return GOL_OK;
+    Plan *P = find_plan(hs, gens, torus);
+    if (!P) {
+        auto np = std::make_unique<Plan>();
+        np->hs = hs;
+        np->gens = gens;
+        np->torus = torus;
+        np->opt_k = g_opt_k;
+        np->opt_rows = g_opt_rows;
+        for (auto h : hs) np->serials.push_back(h->serial);
+        int rc = build_plan(*np);
+        if (rc) return rc;
+        reap(false);
+        g_plans.insert(g_plans.begin(), std::move(np));
+        if (g_plans.size() > kMaxPlans) {
+            bury(std::move(g_plans.back()));
+            g_plans.pop_back();
+        }
+        P = g_plans[0].get();
+    }
+    P->uses++;
+    cudaError_t e;
+    // replays of a repeated batch go through a CUDA graph (not on the legacy stream)
+    if (g_opt_graphs && g_stream != nullptr && P->uses >= 2) {
+        if (!P->graph || P->graph_stream != g_stream) {
+            if (P->graph) {
+                cudaGraphExecDestroy(P->graph);
+                P->graph = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            CU(cudaStreamBeginCapture(g_stream, cudaStreamCaptureModeThreadLocal));
+            e = launch_plan_kernels(*P, g_stream);
+            cudaError_t e2 = cudaStreamEndCapture(g_stream, &graph);
+            if (e != cudaSuccess) return cuda_fail(e, "capturing the step");
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&P->graph, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+            P->graph_stream = g_stream;
+        }
+        e = cudaGraphLaunch(P->graph, g_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    } else {
+        e = launch_plan_kernels(*P, g_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "launching the step");
+    }
+    for (size_t i = 0; i < hs.size(); ++i) {
+        hs[i]->cur ^= (P->npass[i] & 1);
+        hs[i]->generation += gens[i];
+    }
+    return GOL_OK;
+}
+
+int step_bytes(gol_handle h, int64_t G) {
+    for (int64_t g = 0; g < G; ++g) {
+        const uint8_t *in = (const uint8_t *)h->buf[h->cur];
+        uint8_t *out = (uint8_t *)h->buf[h->cur ^ 1];
+        cudaError_t e = launch_byte_step(in, out, h->rows, h->cols, h->torus, g_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "byte step launch");
+        h->cur ^= 1;
+        h->generation += 1;
+    }
+    return GOL_OK;
+}
+
+int set_cur_device(gol_handle h) {
+    CU(cudaMemcpyAsync(h->dev_cur, &h->cur, sizeof(int32_t), cudaMemcpyHostToDevice, g_stream));
+    return GOL_OK;
+}
+
+// split generation counts so that one launch stays within int32 task counts
+constexpr int64_t kMaxGensPerLaunch = int64_t(1) << 24;
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *gol_last_error(void) { return t_err.c_str(); }
+
+int gol_set_stream(void *s) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_stream = (cudaStream_t)s;
+    return GOL_OK;
+}
+
+int gol_set_allocator(void *(*af)(size_t, void *), void (*ff)(void *, void *), void *ctx) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if ((af == nullptr) != (ff == nullptr)) return fail(GOL_EINVAL, "alloc and free must both be set or both null");
+    clear_plans();
+    g_alloc = af;
+    g_free = ff;
+    g_alloc_ctx = ctx;
+    return GOL_OK;
+}
+
+int gol_create_ex(int64_t rows, int64_t cols, int torus, int layout, gol_handle *out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!out) return fail(GOL_EINVAL, "null output handle");
+    *out = nullptr;
+    if (rows < 1 || cols < 1) return fail(GOL_EINVAL, "rows and cols must be >= 1 (got %lld x %lld)",
+                                          (long long)rows, (long long)cols);
+    if (layout == GOL_LAYOUT_AUTO) layout = (cols % 64 == 0) ? GOL_LAYOUT_PACKED : GOL_LAYOUT_BYTES;
+    if (layout != GOL_LAYOUT_PACKED && layout != GOL_LAYOUT_BYTES) return fail(GOL_EINVAL, "unknown layout %d", layout);
+    if (layout == GOL_LAYOUT_PACKED && cols % 64 != 0)
+        return fail(GOL_EINVAL, "packed layout needs cols %% 64 == 0 (cols = %lld)", (long long)cols);
+    if (layout == GOL_LAYOUT_PACKED && (rows > (int64_t(1) << 30) || cols / 64 > (int64_t(1) << 30)))
+        return fail(GOL_EINVAL, "board too large");
+    int rc = ensure_device();
+    if (rc) return rc;
+    auto h = new gol_board();
+    h->rows = rows;
+    h->cols = cols;
+    h->torus = torus ? 1 : 0;
+    h->layout = layout;
+    h->words = layout == GOL_LAYOUT_PACKED ? cols / 64 : 0;
+    h->buf_bytes = layout == GOL_LAYOUT_PACKED ? (size_t)rows * (size_t)h->words * 8 : (size_t)rows * (size_t)cols;
+    h->alloc_fn = g_alloc;
+    h->free_fn = g_free;
+    h->alloc_ctx = g_alloc_ctx;
+    h->serial = ++g_serial;
+    h->buf[0] = dev_alloc(h->buf_bytes, h->alloc_fn, h->alloc_ctx);
+    h->buf[1] = dev_alloc(h->buf_bytes, h->alloc_fn, h->alloc_ctx);
+    h->dev_cur = (int32_t *)dev_alloc(256, h->alloc_fn, h->alloc_ctx);
+    if (!h->buf[0] || !h->buf[1] || !h->dev_cur) {
+        dev_free(h->buf[0], h->free_fn, h->alloc_ctx);
+        dev_free(h->buf[1], h->free_fn, h->alloc_ctx);
+        dev_free(h->dev_cur, h->free_fn, h->alloc_ctx);
+        delete h;
+        return fail(GOL_ENOMEM, "could not allocate 2 x %zu bytes of device memory", (size_t)rows * cols);
+    }
+    cudaError_t e1 = cudaMemsetAsync(h->buf[0], 0, h->buf_bytes, g_stream);
+    cudaError_t e2 = cudaMemsetAsync(h->buf[1], 0, h->buf_bytes, g_stream);
+    cudaError_t e3 = cudaMemsetAsync(h->dev_cur, 0, 256, g_stream);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        dev_free(h->buf[0], h->free_fn, h->alloc_ctx);
+        dev_free(h->buf[1], h->free_fn, h->alloc_ctx);
+        dev_free(h->dev_cur, h->free_fn, h->alloc_ctx);
+        delete h;
+        return cuda_fail(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "clearing a new board");
+    }
+    *out = h;
+    return GOL_OK;
+}
+
+int gol_create(int64_t rows, int64_t cols, int torus, gol_handle *out) {
+    return gol_create_ex(rows, cols, torus, GOL_LAYOUT_AUTO, out);
+}
+
+int gol_destroy(gol_handle h) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!valid(h)) return fail(GOL_EINVAL, "invalid handle");
+    drop_plans_of(h);
+    cudaStreamSynchronize(g_stream);
+    dev_free(h->buf[0], h->free_fn, h->alloc_ctx);
+    dev_free(h->buf[1], h->free_fn, h->alloc_ctx);
+    dev_free(h->dev_cur, h->free_fn, h->alloc_ctx);
+    h->rows = 0;
+    delete h;
+    return GOL_OK;
+}
+
+int gol_info(gol_handle h, int64_t *rows, int64_t *cols, int *torus, int *layout) {
+    if (!valid(h)) return fail(GOL_EINVAL, "invalid handle");
+    if (rows) *rows = h->rows;
+    if (cols) *cols = h->cols;
+    if (torus) *torus = h->torus;
+    if (layout) *layout = h->layout;
+    return GOL_OK;
+}
+
+int gol_set(gol_handle h, const uint8_t *cells, size_t n) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!valid(h) || !cells) return fail(GOL_EINVAL, "invalid handle or null cells");
+    if (n != (size_t)h->rows * (size_t)h->cols)
+        return fail(GOL_EINVAL, "n = %zu, board has %lld cells", n, (long long)(h->rows * h->cols));
+    for (size_t i = 0; i < n; ++i)
+        if (cells[i] > 1) return fail(GOL_EINVAL, "cell %zu has value %u (must be 0 or 1)", i, (unsigned)cells[i]);
+    h->cur = 0;
+    h->generation = 0;
+    if (h->layout == GOL_LAYOUT_BYTES) {
+        CU(cudaMemcpyAsync(h->buf[0], cells, n, cudaMemcpyHostToDevice, g_stream));
+    } else {
+        const size_t flag_off = (n + 255) & ~size_t(255);
+        Scratch st(flag_off + 256);
+        if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", n);
+        int32_t *bad = (int32_t *)((char *)st.p + flag_off);
+        CU(cudaMemsetAsync(bad, 0, sizeof(int32_t), g_stream));
+        CU(cudaMemcpyAsync(st.p, cells, n, cudaMemcpyHostToDevice, g_stream));
+        CU(launch_pack((const uint8_t *)st.p, (uint64_t *)h->buf[0], h->rows, h->words, bad, g_stream));
+        int32_t bad_h = 0;
+        CU(cudaMemcpyAsync(&bad_h, bad, sizeof bad_h, cudaMemcpyDeviceToHost, g_stream));
+        CU(cudaStreamSynchronize(g_stream));
+        if (bad_h) return fail(GOL_EINVAL, "cell values other than 0/1 reached the device");
+    }
+    int rc = set_cur_device(h);
+    if (rc) return rc;
+    return sync_stream();
+}
+
+int gol_get(gol_handle h, uint8_t *cells, size_t n) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!valid(h) || !cells) return fail(GOL_EINVAL, "invalid handle or null cells");
+    if (n != (size_t)h->rows * (size_t)h->cols)
+        return fail(GOL_EINVAL, "n = %zu, board has %lld cells", n, (long long)(h->rows * h->cols));
+    if (h->layout == GOL_LAYOUT_BYTES) {
+        CU(cudaMemcpyAsync(cells, h->buf[h->cur], n, cudaMemcpyDeviceToHost, g_stream));
+        return sync_stream();
+    }
+    Scratch st(n);
+    if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", n);
+    CU(launch_unpack((const uint64_t *)h->buf[h->cur], (uint8_t *)st.p, h->rows, h->words, g_stream));
+    CU(cudaMemcpyAsync(cells, st.p, n, cudaMemcpyDeviceToHost, g_stream));
+    return sync_stream();
+}
+
+int gol_set_packed(gol_handle h, const uint64_t *words, size_t nwords) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!valid(h) || !words) return fail(GOL_EINVAL, "invalid handle or null words");
+    if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board is not packed");
+    if (nwords != (size_t)(h->rows * h->words))
+        return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
+    h->cur = 0;
+    h->generation = 0;
+    CU(cudaMemcpyAsync(h->buf[0], words, nwords * 8, cudaMemcpyHostToDevice, g_stream));
+    return set_cur_device(h);
+}
+
+int gol_get_packed(gol_handle h, uint64_t *words, size_t nwords) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!valid(h) || !words) return fail(GOL_EINVAL, "invalid handle or null words");
+    if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board is not packed");
+    if (nwords != (size_t)(h->rows * h->words))
+        return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
+    CU(cudaMemcpyAsync(words, h->buf[h->cur], nwords * 8, cudaMemcpyDeviceToHost, g_stream));
+    return sync_stream();
+}
+
+int gol_set_packed_device(gol_handle h, const uint64_t *dwords, size_t nwords) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!valid(h) || !dwords) return fail(GOL_EINVAL, "invalid handle or null words");
+    if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board is not packed");
+    if (nwords != (size_t)(h->rows * h->words))
+        return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
+    h->cur = 0;
+    h->generation = 0;
+    CU(cudaMemcpyAsync(h->buf[0], dwords, nwords * 8, cudaMemcpyDeviceToDevice, g_stream));
+    return set_cur_device(h);
+}
+
+int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!valid(h) || !dwords) return fail(GOL_EINVAL, "invalid handle or null words");
+    if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board is not packed");
+    if (nwords != (size_t)(h->rows * h->words))
+        return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
+    CU(cudaMemcpyAsync(dwords, h->buf[h->cur], nwords * 8, cudaMemcpyDeviceToDevice, g_stream));
+    return GOL_OK;
+}
+
+int gol_get_region(gol_handle h, int64_t r0, int64_t c0, int64_t nr, int64_t nc, uint8_t *out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!valid(h)) return fail(GOL_EINVAL, "invalid handle");
+    if (nr < 0 || nc < 0) return fail(GOL_EINVAL, "negative window size");
+    if (nr == 0 || nc == 0) return GOL_OK;
+    if (!out) return fail(GOL_EINVAL, "null output");
+    const size_t n = (size_t)nr * (size_t)nc;
+    Scratch st(n);
+    if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", n);
+    if (h->layout == GOL_LAYOUT_PACKED)
+        CU(launch_region_packed((const uint64_t *)h->buf[h->cur], h->rows, h->words, r0, c0, nr, nc,
+                                (uint8_t *)st.p, g_stream));
+    else
+        CU(launch_region_bytes((const uint8_t *)h->buf[h->cur], h->rows, h->cols, r0, c0, nr, nc,
+                               (uint8_t *)st.p, g_stream));
+    CU(cudaMemcpyAsync(out, st.p, n, cudaMemcpyDeviceToHost, g_stream));
+    return sync_stream();
+}
+
+int gol_step(gol_handle h, int64_t generations) {
+    gol_handle hs[1] = {h};
+    int64_t gs[1] = {generations};
+    return gol_step_batch(hs, gs, 1);
+}
+
+int gol_step_batch(const gol_handle *hs, const int64_t *generations, size_t n) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (n == 0) return GOL_OK;
+    if (!hs || !generations) return fail(GOL_EINVAL, "null arrays");
+    std::unordered_set<gol_handle> seen;
+    for (size_t i = 0; i < n; ++i) {
+        if (!valid(hs[i])) return fail(GOL_EINVAL, "invalid handle at %zu", i);
+        if (generations[i] < 0) return fail(GOL_EINVAL, "negative generation count at %zu", i);
+        if (!seen.insert(hs[i]).second) return fail(GOL_EINVAL, "handle repeated at %zu", i);
+    }
+    // byte boards one by one
+    for (size_t i = 0; i < n; ++i)
+        if (hs[i]->layout == GOL_LAYOUT_BYTES && generations[i] > 0) {
+            int rc = step_bytes(hs[i], generations[i]);
+            if (rc) return rc;
+        }
+    // packed boards: torus and bounded groups, split into launches of at most
+    // kMaxGensPerLaunch generations
+    for (int torus = 1; torus >= 0; --torus) {
+        std::vector<gol_handle> grp;
+        std::vector<int64_t> left;
+        for (size_t i = 0; i < n; ++i)
+            if (hs[i]->layout == GOL_LAYOUT_PACKED && hs[i]->torus == torus && generations[i] > 0) {
+                grp.push_back(hs[i]);
+                left.push_back(generations[i]);
+            }
+        while (!grp.empty()) {
+            std::vector<gol_handle> now;
+            std::vector<int64_t> g;
+            for (size_t i = 0; i < grp.size(); ++i) {
+                const int64_t take = std::min(left[i], kMaxGensPerLaunch);
+                now.push_back(grp[i]);
+                g.push_back(take);
+                left[i] -= take;
+            }
+            int rc = run_packed(now, g, torus == 1);
+            if (rc) return rc;
+            std::vector<gol_handle> g2;
+            std::vector<int64_t> l2;
+            for (size_t i = 0; i < grp.size(); ++i)
+                if (left[i] > 0) {
+                    g2.push_back(grp[i]);
+                    l2.push_back(left[i]);
+                }
+            grp.swap(g2);
+            left.swap(l2);
+        }
+    }
+    return GOL_OK;
+}
+
+int gol_population(gol_handle h, uint64_t *out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!valid(h) || !out) return fail(GOL_EINVAL, "invalid handle or null output");
+    Scratch st(sizeof(unsigned long long));
+    if (!st.p) return fail(GOL_ENOMEM, "population scratch");
+    CU(cudaMemsetAsync(st.p, 0, sizeof(unsigned long long), g_stream));
+    if (h->layout == GOL_LAYOUT_PACKED)
+        CU(launch_popcount_packed((const uint64_t *)h->buf[h->cur], h->rows * h->words,
+                                  (unsigned long long *)st.p, g_stream));
+    else
+        CU(launch_popcount_bytes((const uint8_t *)h->buf[h->cur], h->rows * h->cols,
+                                 (unsigned long long *)st.p, g_stream));
+    unsigned long long v = 0;
+    CU(cudaMemcpyAsync(&v, st.p, sizeof v, cudaMemcpyDeviceToHost, g_stream));
+    int rc = sync_stream();
+    if (rc) return rc;
+    *out = v;
+    return GOL_OK;
+}
+
+int gol_generation(gol_handle h, int64_t *out) {
+    if (!valid(h) || !out) return fail(GOL_EINVAL, "invalid handle or null output");
+    *out = h->generation;
+    return GOL_OK;
+}
+
+int gol_sync(gol_handle h) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!valid(h)) return fail(GOL_EINVAL, "invalid handle");
+    return sync_stream();
+}
+
+int gol_set_option(int key, int64_t v) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    switch (key) {
+        case GOL_OPT_GENS_PER_PASS:
+            if (!(v == 0 || v == 1 || v == 2 || v == 4 || v == 8 || v == 16))
+                return fail(GOL_EINVAL, "generations per pass must be 0, 1, 2, 4, 8 or 16");
+            g_opt_k = v;
+            return GOL_OK;
+        case GOL_OPT_TILE_ROWS:
+            if (v < 0 || v > (1 << 20)) return fail(GOL_EINVAL, "tile rows out of range");
+            g_opt_rows = v;
+            return GOL_OK;
+        case GOL_OPT_USE_GRAPHS:
+            g_opt_graphs = v ? 1 : 0;
+            return GOL_OK;
+        case GOL_OPT_WAIT_TIMEOUT_MS:
+            if (v < 1 || v > 3600000) return fail(GOL_EINVAL, "timeout out of range");
+            g_opt_timeout_ms = v;
+            return GOL_OK;
+    }
+    return fail(GOL_EINVAL, "unknown option %d", key);
+}
+
+int gol_get_option(int key, int64_t *v) {
+    if (!v) return fail(GOL_EINVAL, "null output");
+    switch (key) {
+        case GOL_OPT_GENS_PER_PASS: *v = g_opt_k; return GOL_OK;
+        case GOL_OPT_TILE_ROWS: *v = g_opt_rows; return GOL_OK;
+        case GOL_OPT_USE_GRAPHS: *v = g_opt_graphs; return GOL_OK;
+        case GOL_OPT_WAIT_TIMEOUT_MS: *v = g_opt_timeout_ms; return GOL_OK;
+    }
+    return fail(GOL_EINVAL, "unknown option %d", key);
+}
+
+int gol_tune_set(int64_t rows, int64_t cols, int k, int tile_rows) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (rows < 1 || cols < 1 || k < 1 || k > 16 || (k & (k - 1)) || tile_rows < 1)
+        return fail(GOL_EINVAL, "bad tune entry");
+    g_tune[size_class(rows, cols)] = TuneEntry{k, tile_rows};
+    clear_plans();
+    return GOL_OK;
+}
+
+int gol_tune_get(int64_t rows, int64_t cols, int *k, int *tile_rows) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (rows < 1 || cols < 1) return fail(GOL_EINVAL, "bad size");
+    TuneEntry t = tune_lookup(rows, cols);
+    if (k) *k = supported_k(t.k);
+    if (tile_rows) *tile_rows = t.rows;
+    return GOL_OK;
+}
+
+int gol_device_info(int *sms, int64_t *l2, int *clk) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int rc = ensure_device();
+    if (rc) return rc;
+    if (sms) *sms = g_dev.sms;
+    if (l2) *l2 = g_dev.l2;
+    if (clk) *clk = g_dev.clock_khz;
+    return GOL_OK;
+}
+
+int gol_probe_int_throughput(double *ops_per_s, double *seconds) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int rc = ensure_device();
+    if (rc) return rc;
+    const int block = 256, iters = 20000;
+    const int grid = g_dev.sms * 8;
+    Scratch sink((size_t)grid * 4);
+    if (!sink.p) return fail(GOL_ENOMEM, "probe sink");
+    cudaEvent_t a, b;
+    CU(cudaEventCreate(&a));
+    CU(cudaEventCreate(&b));
+    CU(launch_int_probe((unsigned *)sink.p, 100, grid, block, g_stream));   // warm-up
+    CU(cudaEventRecord(a, g_stream));
+    CU(launch_int_probe((unsigned *)sink.p, iters, grid, block, g_stream));
+    CU(cudaEventRecord(b, g_stream));
+    CU(cudaEventSynchronize(b));
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    const double ops = (double)grid * block * iters * int_probe_ops_per_iter();
+    if (ops_per_s) *ops_per_s = ops / (ms * 1e-3);
+    if (seconds) *seconds = ms * 1e-3;
+    return GOL_OK;
+}
+
+int gol_debug_unfilled_wait(int64_t timeout_ms) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int rc = ensure_device();
+    if (rc) return rc;
+    if (timeout_ms < 1 || timeout_ms > 60000) return fail(GOL_EINVAL, "timeout out of range");
+    Scratch ws(4096);
+    if (!ws.p) return fail(GOL_ENOMEM, "debug workspace");
+    PersistArgs a{};
+    char *base = (char *)ws.p;
+    a.boards = nullptr;
+    a.units = nullptr;
+    a.done = (int32_t *)(base + 0);
+    a.claimed = (int32_t *)(base + 256);
+    a.ctr = (int32_t *)(base + 512);
+    a.ring = (int32_t *)(base + 1024);
+    a.sticky = g_dev.sticky;
+    a.nunits = 0;        // no work ...
+    a.total_tasks = 1;   // ... but one ticket: its slot is never filled
+    a.timeout_ns = timeout_ms * 1000000ll;
+    CU(launch_sched_init(a, 0, g_stream));
+    CU(launch_persistent<1>(a, true, 1, g_stream));
+    CU(cudaStreamSynchronize(g_stream));
+    int32_t status = 0;
+    CU(cudaMemcpy(&status, a.ctr + 3, sizeof status, cudaMemcpyDeviceToHost));
+    int rc2 = take_sticky();
+    if (status == GOL_ETIMEOUT && rc2 == GOL_ETIMEOUT) return GOL_ETIMEOUT;
+    return fail(GOL_ECUDA, "bounded wait did not report a timeout (status %d, sticky %d)", status, rc2);
+}
+
+}  // extern "C"

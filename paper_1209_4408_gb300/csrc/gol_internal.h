@@ -1,0 +1,97 @@
+// Internal declarations shared by the library's translation units.
+//
+// Packed boards: R rows of W uint64 words, row major, no padding; bit j of
+// word k holds column 64k + j.  Each board owns two such buffers and a
+// device int `cur` naming the one that holds the current generation.
+//
+// A packed step is organised in "units": the rectangle of output cells one
+// warp produces per pass.  A pass advances a unit by kk <= K generations,
+// reading the previous pass's buffer (with a K-row and one-word halo) and
+// writing the other buffer.  Passes of neighbouring units are ordered by
+// the dataflow scheduler in wavefront.cuh.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gol.h"
+
+namespace gol {
+
+constexpr int kMaxNeighbours = 8;   // units whose output a unit's halo can touch
+constexpr int kTileWords = 30;      // output words of a tiled warp (32 lanes - 2 halo lanes)
+constexpr int kWarpsPerBlock = 4;   // persistent kernel: 128-thread blocks
+
+enum UnitMode : int32_t { kUnitFull = 0, kUnitTiled = 1 };
+
+// One board in a launch (device memory).
+struct BoardDesc {
+    uint64_t *buf[2];
+    int32_t *cur;     // device: index of the buffer holding the current state
+    int32_t R;        // rows
+    int32_t W;        // words per row
+    int32_t npass;    // passes in this launch (>= 1)
+    int32_t gens;     // generations in this launch (>= npass)
+    int32_t nunits;   // units of this board
+    int32_t pad;
+};
+
+// One unit (device memory).
+//  kUnitFull : W <= 32, a row fits one warp; lanes are S segments of W
+//              lanes, segment s produces rows [r0 + s*H, r0 + (s+1)*H)
+//              clipped to r_end; horizontal wrap happens inside the segment.
+//  kUnitTiled: W > 32; lane l holds word (w0 - 1 + l) mod W for l < U + 2,
+//              lanes 1..U produce words w0 .. w0+U-1 of rows [r0, r_end).
+struct UnitDesc {
+    int32_t board;
+    int32_t r0, r_end;
+    int32_t H;        // segment height
+    int32_t S;        // segments (kUnitFull) or 1
+    int32_t w0, U;    // kUnitTiled word range; kUnitFull: 0, W
+    int32_t mode;
+    int32_t nnb;      // neighbour units (same board), whose passes bound this one's
+    int32_t nb[kMaxNeighbours];
+    int32_t pad;
+};
+
+// Kernel arguments of the persistent dataflow kernel.
+struct PersistArgs {
+    const BoardDesc *boards;
+    const UnitDesc *units;
+    int32_t *done;      // [nunits] passes completed
+    int32_t *claimed;   // [nunits] passes claimed (== done when idle)
+    int32_t *ring;      // [total_tasks] work queue, -1 = empty slot
+    int32_t *ctr;       // [0] head ticket, [1] tail slot, [2] tasks completed, [3] status,
+                        // [4 + b] units of board b that finished all passes
+    int32_t *sticky;    // process-wide error word read by synchronising calls
+    int32_t nunits;
+    int32_t total_tasks;
+    int64_t timeout_ns; // bounded waits give up after this long without progress
+};
+
+// Launchers (one translation unit per K).  Return cudaGetLastError().
+template <int K>
+cudaError_t launch_persistent(const PersistArgs &a, bool torus, int grid, cudaStream_t s);
+template <int K>
+cudaError_t persistent_occupancy(bool torus, int *blocks_per_sm);
+
+// Utility kernels (kernels_util.cu).
+cudaError_t launch_sched_init(const PersistArgs &a, int nboards, cudaStream_t s);
+cudaError_t launch_byte_step(const uint8_t *in, uint8_t *out, int64_t R, int64_t C, int torus,
+                             cudaStream_t s);
+cudaError_t launch_pack(const uint8_t *cells, uint64_t *words, int64_t R, int64_t W, int32_t *bad,
+                        cudaStream_t s);
+cudaError_t launch_check_bytes(const uint8_t *cells, int64_t n, int32_t *bad, cudaStream_t s);
+cudaError_t launch_unpack(const uint64_t *words, uint8_t *cells, int64_t R, int64_t W, cudaStream_t s);
+cudaError_t launch_region_packed(const uint64_t *words, int64_t R, int64_t W, int64_t r0, int64_t c0,
+                                 int64_t nr, int64_t nc, uint8_t *out, cudaStream_t s);
+cudaError_t launch_region_bytes(const uint8_t *cells, int64_t R, int64_t C, int64_t r0, int64_t c0,
+                                int64_t nr, int64_t nc, uint8_t *out, cudaStream_t s);
+cudaError_t launch_popcount_packed(const uint64_t *words, int64_t n, unsigned long long *out,
+                                   cudaStream_t s);
+cudaError_t launch_popcount_bytes(const uint8_t *cells, int64_t n, unsigned long long *out,
+                                  cudaStream_t s);
+cudaError_t launch_int_probe(unsigned *sink, int iters, int grid, int block, cudaStream_t s);
+int int_probe_ops_per_iter();   // 32-bit integer operations per thread per probe iteration
+
+}  // namespace gol

@@ -1,0 +1,268 @@
+// Byte-per-cell step, layout conversion, population count, scheduler
+// initialisation and the integer-throughput probe.
+#include "gol_internal.h"
+#include "wavefront.cuh"
+
+namespace gol {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+int grid_for(int64_t n, int block = kBlock, int64_t cap = 1 << 20) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// --- scheduler state ------------------------------------------------------
+__global__ void sched_init_kernel(PersistArgs a, int nboards) {
+    const int64_t n = max(max((int64_t)a.nunits, (int64_t)a.total_tasks), (int64_t)nboards);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < a.nunits) {
+            a.done[i] = 0;
+            a.claimed[i] = 1;   // every unit's first pass is queued below
+        }
+        if (i < a.total_tasks) a.ring[i] = i < a.nunits ? (int32_t)i : -1;
+        if (i < nboards) a.ctr[4 + i] = 0;
+        if (i == 0) {
+            a.ctr[0] = 0;         // next ticket
+            a.ctr[1] = a.nunits;  // next free slot
+            a.ctr[2] = 0;         // tasks completed
+            a.ctr[3] = 0;         // status
+        }
+    }
+}
+
+// --- byte-per-cell step (Section 1, one uint8 per cell) -------------------
+__global__ void byte_step_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out,
+                                 int64_t R, int64_t C, int torus) {
+    const int64_t n = R * C;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / C, c = i - r * C;
+        int cnt = 0;
+#pragma unroll
+        for (int dr = -1; dr <= 1; ++dr) {
+            int64_t rr = r + dr;
+            bool rin = true;
+            if (rr < 0) {
+                rr = R - 1;
+                rin = torus;
+            } else if (rr >= R) {
+                rr = 0;
+                rin = torus;
+            }
+#pragma unroll
+            for (int dc = -1; dc <= 1; ++dc) {
+                if (dr == 0 && dc == 0) continue;
+                int64_t cc = c + dc;
+                bool cin = true;
+                if (cc < 0) {
+                    cc = C - 1;
+                    cin = torus;
+                } else if (cc >= C) {
+                    cc = 0;
+                    cin = torus;
+                }
+                if (rin && cin) cnt += in[rr * C + cc] != 0;
+            }
+        }
+        const bool alive = in[i] != 0;
+        out[i] = (cnt == 3) || (alive && cnt == 2);
+    }
+}
+
+// --- layout conversion ------------------------------------------------------
+// four 0/1 bytes of a little-endian uint32 -> 4 bits
+__device__ __forceinline__ uint32_t gather4(uint32_t x) {
+    return (x | (x >> 7) | (x >> 14) | (x >> 21)) & 0xFu;
+}
+__device__ __forceinline__ uint32_t spread4(uint32_t b) {
+    return (b & 1u) | ((b & 2u) << 7) | ((b & 4u) << 14) | ((b & 8u) << 21);
+}
+
+__global__ void pack_kernel(const uint8_t *__restrict__ cells, uint64_t *__restrict__ words,
+                            int64_t nwords, int32_t *bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(cells + i * 64);
+        uint64_t w = 0;
+        uint32_t any_high = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 v = p[q];
+            const uint32_t parts[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                any_high |= parts[e] & 0xFEFEFEFEu;
+                w |= (uint64_t)gather4(parts[e]) << (16 * q + 4 * e);
+            }
+        }
+        if (any_high) atomicExch(bad, 1);
+        words[i] = w;
+    }
+}
+
+__global__ void check_bytes_kernel(const uint8_t *__restrict__ cells, int64_t n, int32_t *bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (cells[i] > 1) atomicExch(bad, 1);
+}
+
+__global__ void unpack_kernel(const uint64_t *__restrict__ words, uint8_t *__restrict__ cells,
+                              int64_t nwords) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t w = words[i];
+        uint4 *p = reinterpret_cast<uint4 *>(cells + i * 64);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint4 v;
+            v.x = spread4((uint32_t)(w >> (16 * q + 0)) & 0xFu);
+            v.y = spread4((uint32_t)(w >> (16 * q + 4)) & 0xFu);
+            v.z = spread4((uint32_t)(w >> (16 * q + 8)) & 0xFu);
+            v.w = spread4((uint32_t)(w >> (16 * q + 12)) & 0xFu);
+            p[q] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ int64_t wrap(int64_t x, int64_t m) {
+    int64_t r = x % m;
+    return r < 0 ? r + m : r;
+}
+
+__global__ void region_packed_kernel(const uint64_t *__restrict__ words, int64_t R, int64_t W,
+                                     int64_t r0, int64_t c0, int64_t nr, int64_t nc,
+                                     uint8_t *__restrict__ out) {
+    const int64_t n = nr * nc, C = W * 64;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t y = i / nc, x = i - y * nc;
+        const int64_t r = wrap(r0 + y, R), c = wrap(c0 + x, C);
+        out[i] = (uint8_t)((words[r * W + (c >> 6)] >> (c & 63)) & 1u);
+    }
+}
+
+__global__ void region_bytes_kernel(const uint8_t *__restrict__ cells, int64_t R, int64_t C,
+                                    int64_t r0, int64_t c0, int64_t nr, int64_t nc,
+                                    uint8_t *__restrict__ out) {
+    const int64_t n = nr * nc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t y = i / nc, x = i - y * nc;
+        out[i] = cells[wrap(r0 + y, R) * C + wrap(c0 + x, C)];
+    }
+}
+
+template <typename T>
+__global__ void popcount_kernel(const T *__restrict__ v, int64_t n, unsigned long long *out) {
+    unsigned long long s = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (sizeof(T) == 8)
+            s += __popcll((unsigned long long)v[i]);
+        else
+            s += v[i] != 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+// --- integer-pipe probe -------------------------------------------------------
+// Eight independent chains; per iteration and chain five LOP3 and one funnel
+// shift, the 20:4 LOP3:SHF ratio of one generation of a word.
+constexpr int kProbeChains = 8;
+constexpr int kProbeOpsPerChain = 6;
+
+__global__ void int_probe_kernel(unsigned *sink, int iters) {
+    uint32_t x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) x[c] = threadIdx.x * 0x9E3779B9u + c * 0x85EBCA6Bu + blockIdx.x;
+    uint32_t y = threadIdx.x ^ 0x5bd1e995u, z = blockIdx.x ^ 0x27d4eb2fu;
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c) {
+            uint32_t v = x[c];
+            v = lop3<0x96>(v, y, z);
+            v = lop3<0xE8>(v, z, y);
+            v = lop3<0x14>(v, y, z);
+            v = __funnelshift_l(v, y, 1 + (c & 3));
+            v = lop3<0x82>(v, z, y);
+            v = lop3<0xCA>(v, y, z);
+            x[c] = v;
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) acc ^= x[c];
+    if (acc == 0x12345678u) sink[blockIdx.x] = acc;   // keeps the chains live
+}
+
+}  // namespace
+
+cudaError_t launch_sched_init(const PersistArgs &a, int nboards, cudaStream_t s) {
+    const int64_t n = max(max((int64_t)a.nunits, (int64_t)a.total_tasks), (int64_t)max(nboards, 1));
+    sched_init_kernel<<<grid_for(n, kBlock, 4096), kBlock, 0, s>>>(a, nboards);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_byte_step(const uint8_t *in, uint8_t *out, int64_t R, int64_t C, int torus,
+                             cudaStream_t s) {
+    byte_step_kernel<<<grid_for(R * C), kBlock, 0, s>>>(in, out, R, C, torus);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const uint8_t *cells, uint64_t *words, int64_t R, int64_t W, int32_t *bad,
+                        cudaStream_t s) {
+    pack_kernel<<<grid_for(R * W), kBlock, 0, s>>>(cells, words, R * W, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_bytes(const uint8_t *cells, int64_t n, int32_t *bad, cudaStream_t s) {
+    check_bytes_kernel<<<grid_for(n), kBlock, 0, s>>>(cells, n, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const uint64_t *words, uint8_t *cells, int64_t R, int64_t W, cudaStream_t s) {
+    unpack_kernel<<<grid_for(R * W), kBlock, 0, s>>>(words, cells, R * W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_region_packed(const uint64_t *words, int64_t R, int64_t W, int64_t r0, int64_t c0,
+                                 int64_t nr, int64_t nc, uint8_t *out, cudaStream_t s) {
+    region_packed_kernel<<<grid_for(nr * nc), kBlock, 0, s>>>(words, R, W, r0, c0, nr, nc, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_region_bytes(const uint8_t *cells, int64_t R, int64_t C, int64_t r0, int64_t c0,
+                                int64_t nr, int64_t nc, uint8_t *out, cudaStream_t s) {
+    region_bytes_kernel<<<grid_for(nr * nc), kBlock, 0, s>>>(cells, R, C, r0, c0, nr, nc, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_popcount_packed(const uint64_t *words, int64_t n, unsigned long long *out,
+                                   cudaStream_t s) {
+    popcount_kernel<uint64_t><<<grid_for(n, kBlock, 8192), kBlock, 0, s>>>(words, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_popcount_bytes(const uint8_t *cells, int64_t n, unsigned long long *out,
+                                  cudaStream_t s) {
+    popcount_kernel<uint8_t><<<grid_for(n, kBlock, 8192), kBlock, 0, s>>>(cells, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_int_probe(unsigned *sink, int iters, int grid, int block, cudaStream_t s) {
+    int_probe_kernel<<<grid, block, 0, s>>>(sink, iters);
+    return cudaGetLastError();
+}
+
+int int_probe_ops_per_iter() { return kProbeChains * kProbeOpsPerChain; }
+
+}  // namespace gol

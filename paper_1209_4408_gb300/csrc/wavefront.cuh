@@ -1,0 +1,414 @@
+// Packed Game of Life step: a register wavefront over bit-sliced words,
+// run by a persistent dataflow scheduler.
+//
+// Arithmetic (Section 1 of the paper).  A lane holds one 64-cell word of a
+// row as two 32-bit halves.  For an input row it forms the row's
+// horizontal three-cell sum per column as two bit planes:
+//     Wv = row shifted so bit j holds column j-1 (funnel shift, the carry bit
+//          comes from the west word, fetched from the neighbouring lane)
+//     Ev = row shifted so bit j holds column j+1
+//     s0 = Wv ^ x ^ Ev,  s1 = majority(Wv, x, Ev)          (s = s0 + 2 s1)
+// The nine-cell sum of a cell is S = s(row above) + s(row) + s(row below),
+// which includes the cell itself, so with n = S - alive the four
+// transitions reduce to  next = (S == 3) | (alive & (S == 4)).  That
+// predicate is evaluated bit-sliced with eight 3-input LOP3 operations per
+// 32-bit half (rule32).  One generation of a word costs 4 funnel shifts +
+// 20 LOP3 = 24 integer operations and 2 warp shuffles.
+//
+// Temporal blocking.  A warp streams the rows of its unit top to bottom
+// through K pipeline stages held in registers; stage g turns generation g
+// rows into generation g+1 rows, keeping a three-row window (two row sums
+// and one alive word).  A unit with H output rows per segment reads
+// H + 2K input rows of the previous buffer (a K-row halo above and below,
+// taken modulo R on the torus) and writes H rows of generation kk <= K.
+// Stages g >= kk pass rows through unchanged, so one kernel serves passes
+// of any length up to K.  Horizontally the validity of a tiled warp shrinks
+// by one cell per generation from each side, so one halo word per side is
+// exact for K <= 64.
+//
+// Scheduling.  A unit's pass p reads pass p-1 output of every unit whose
+// output its halo touches (its neighbours) and overwrites the buffer those
+// units read during pass p-1; it may start once all of them have completed
+// pass p-1.  Warps take work from a global queue (tickets on head, slots
+// filled in order); after a pass a warp publishes done[u] = p, issues a
+// sequentially consistent fence and re-examines u and its neighbours: a unit
+// whose neighbours have all caught up is claimed with a CAS on claimed[] and
+// either run next by the same warp or appended to the queue.  The fence
+// makes the last of several concurrent completers see all their stores, so
+// no ready unit is missed.  Every wait is bounded: a waiter gives up after
+// `timeout_ns` without any task completing, records GOL_ETIMEOUT and
+// returns.
+#pragma once
+
+#include <type_traits>
+
+#include "gol_internal.h"
+
+namespace gol {
+
+template <unsigned LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+}
+
+// LUT constants: f(0xF0, 0xCC, 0xAA) for operands (a, b, c).
+constexpr unsigned kXor3 = 0x96;   // a ^ b ^ c
+constexpr unsigned kMaj3 = 0xE8;   // majority(a, b, c)
+
+// Next state of 32 cells from the row-sum planes of the rows above (t),
+// at (m) and below (b) and the alive bits a of the middle row.
+//   t0+m0+b0 = u0 + 2 u1,  t1+m1+b1 = p + 2 q  =>  S = u0 + 2 (u1 + p) + 4 q
+//   S == 3      <=> u0 & (p ^ u1) & ~q
+//   S == 4      <=> ~u0 & ~(p ^ u1) & (p ^ q)
+__device__ __forceinline__ uint32_t rule32(uint32_t t0, uint32_t t1, uint32_t m0, uint32_t m1,
+                                           uint32_t b0, uint32_t b1, uint32_t a) {
+    const uint32_t u0 = lop3<kXor3>(t0, m0, b0);
+    const uint32_t u1 = lop3<kMaj3>(t0, m0, b0);
+    const uint32_t p = lop3<kXor3>(t1, m1, b1);
+    const uint32_t q = lop3<kMaj3>(t1, m1, b1);
+    const uint32_t x3 = lop3<0x14>(p, u1, q);   // (p ^ u1) & ~q
+    const uint32_t y1 = lop3<0x82>(p, u1, a);   // ~(p ^ u1) & a
+    const uint32_t y4 = lop3<0x60>(y1, p, q);   // y1 & (p ^ q)
+    return lop3<0xCA>(u0, x3, y4);              // u0 ? x3 : y4
+}
+
+// ---------------------------------------------------------------------------
+// memory-model helpers (PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire(const int32_t *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int32_t *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_sc_gpu() { asm volatile("fence.sc.gpu;" ::: "memory"); }
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint2 ld_cg_u64(const uint64_t *p) {
+    uint2 v;
+    asm volatile("ld.global.cg.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_u64(uint64_t *p, uint32_t lo, uint32_t hi) {
+    asm volatile("st.global.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(lo), "r"(hi) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// One pass of one unit by one warp.
+// ---------------------------------------------------------------------------
+template <int K, bool TORUS>
+__device__ __forceinline__ void run_unit_pass(const BoardDesc &bd, const UnitDesc &ud,
+                                              const uint64_t *__restrict__ src,
+                                              uint64_t *__restrict__ dst, int kk) {
+    constexpr unsigned kFull = 0xffffffffu;
+    constexpr int PF = (2 * K) % 4 == 0 ? 4 : 2;   // rows prefetched ahead
+    constexpr int NPRO = 2 * K;                    // prologue iterations
+    const int lane = threadIdx.x & 31;
+    const int R = bd.R, W = bd.W;
+
+    // ---- lane geometry -------------------------------------------------
+    int seg = 0, word = 0, west_src = lane, east_src = lane;
+    bool loads = false, stores = false;
+    uint32_t west_mask = ~0u, east_mask = ~0u, lane_mask = ~0u;
+    if (ud.mode == kUnitFull) {
+        seg = lane / W;
+        word = lane - seg * W;
+        if (seg < ud.S) {
+            loads = stores = true;
+            const int base = lane - word;
+            west_src = base + (word == 0 ? W - 1 : word - 1);
+            east_src = base + (word == W - 1 ? 0 : word + 1);
+            if (!TORUS) {
+                if (word == 0) west_mask = 0;
+                if (word == W - 1) east_mask = 0;
+            }
+        } else {
+            seg = 0;
+            word = 0;
+        }
+    } else {
+        int w = ud.w0 - 1 + lane;
+        loads = lane < ud.U + 2;
+        stores = lane >= 1 && lane <= ud.U;
+        if (TORUS) {
+            w = w < 0 ? w + W : (w >= W ? w - W : w);
+        } else if (w < 0 || w >= W) {
+            lane_mask = 0;
+            loads = false;
+            w = 0;
+        }
+        word = loads ? w : 0;
+        west_src = lane == 0 ? 0 : lane - 1;
+        east_src = lane == 31 ? 31 : lane + 1;
+    }
+    const int a = ud.r0 + seg * ud.H;                       // first output row of the segment
+    const int seg_end = min(a + ud.H, ud.r_end);            // one past its last output row
+    const int nmain = ud.H;                                 // main-loop iterations
+
+    // ---- input row stream: row (a - K + j) of src ---------------------
+    int lrow = a - K;                                       // row of the next load (unwrapped)
+    int lwrap = lrow;                                       // wrapped row
+    if (TORUS) {
+        lwrap %= R;
+        if (lwrap < 0) lwrap += R;
+    }
+    const uint64_t *colp = src + word;
+    auto load_next = [&](uint32_t &lo, uint32_t &hi) {
+        lo = hi = 0;
+        if (TORUS) {
+            if (loads) {
+                const uint2 v = ld_cg_u64(colp + (size_t)lwrap * W);
+                lo = v.x;
+                hi = v.y;
+            }
+            if (++lwrap == R) lwrap = 0;
+        } else {
+            if (loads && lrow >= 0 && lrow < R) {
+                const uint2 v = ld_cg_u64(colp + (size_t)lrow * W);
+                lo = v.x;
+                hi = v.y;
+            }
+        }
+        ++lrow;
+    };
+
+    // ---- pipeline registers ----------------------------------------------
+    uint32_t p0l[K], p0h[K], p1l[K], p1h[K];   // row sum two rows back
+    uint32_t c0l[K], c0h[K], c1l[K], c1h[K];   // row sum one row back
+    uint32_t cal[K], cah[K];                   // alive word one row back
+#pragma unroll
+    for (int g = 0; g < K; ++g) {
+        p0l[g] = p0h[g] = p1l[g] = p1h[g] = 0;
+        c0l[g] = c0h[g] = c1l[g] = c1h[g] = 0;
+        cal[g] = cah[g] = 0;
+    }
+    uint32_t fl[PF], fh[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) load_next(fl[u], fh[u]);
+
+    // One iteration: the gen-0 row (a - K + j) enters stage 0; returns the
+    // generation-kk row (a + j - 2K) leaving the last stage.  In the
+    // prologue (GUARD) stage g only runs once its window holds valid rows.
+    auto iterate = [&](uint32_t xl, uint32_t xh, int j, auto guard_tag) {
+        constexpr bool GUARD = decltype(guard_tag)::value;
+        const int jr = a - K + j;
+#pragma unroll
+        for (int g = 0; g < K; ++g) {
+            if (GUARD && j < 2 * g) break;                  // input of stage g not produced yet
+            const uint32_t wh = __shfl_sync(kFull, xh, west_src) & west_mask;
+            const uint32_t el = __shfl_sync(kFull, xl, east_src) & east_mask;
+            const uint32_t Wl = __funnelshift_l(wh, xl, 1);
+            const uint32_t Wh = __funnelshift_l(xl, xh, 1);
+            const uint32_t El = __funnelshift_r(xl, xh, 1);
+            const uint32_t Eh = __funnelshift_r(xh, el, 1);
+            const uint32_t n0l = lop3<kXor3>(Wl, xl, El), n0h = lop3<kXor3>(Wh, xh, Eh);
+            const uint32_t n1l = lop3<kMaj3>(Wl, xl, El), n1h = lop3<kMaj3>(Wh, xh, Eh);
+            uint32_t ol = 0, oh = 0;
+            if (!GUARD || j >= 2 * g + 2) {
+                ol = rule32(p0l[g], p1l[g], c0l[g], c1l[g], n0l, n1l, cal[g]);
+                oh = rule32(p0h[g], p1h[g], c0h[g], c1h[g], n0h, n1h, cah[g]);
+                if (g >= kk) {                              // pass shorter than K: identity stage
+                    ol = cal[g];
+                    oh = cah[g];
+                }
+                if (!TORUS) {
+                    const bool inside = (unsigned)(jr - g - 1) < (unsigned)R;
+                    ol = inside ? (ol & lane_mask) : 0u;
+                    oh = inside ? (oh & lane_mask) : 0u;
+                }
+            }
+            p0l[g] = c0l[g];
+            p0h[g] = c0h[g];
+            p1l[g] = c1l[g];
+            p1h[g] = c1h[g];
+            c0l[g] = n0l;
+            c0h[g] = n0h;
+            c1l[g] = n1l;
+            c1h[g] = n1h;
+            cal[g] = xl;
+            cah[g] = xh;
+            xl = ol;
+            xh = oh;
+        }
+        return make_uint2(xl, xh);
+    };
+
+#pragma unroll 1
+    for (int j0 = 0; j0 < NPRO; j0 += PF) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const uint32_t xl = fl[u], xh = fh[u];
+            load_next(fl[u], fh[u]);
+            iterate(xl, xh, j0 + u, std::true_type{});
+        }
+    }
+    int orow = a;                                           // row of the next output
+    uint64_t *outp = dst + word;
+#pragma unroll 1
+    for (int j0 = 0; j0 < nmain; j0 += PF) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const uint32_t xl = fl[u], xh = fh[u];
+            load_next(fl[u], fh[u]);
+            const uint2 o = iterate(xl, xh, NPRO + j0 + u, std::false_type{});
+            if (stores && orow < seg_end) st_u64(outp + (size_t)orow * W, o.x, o.y);
+            ++orow;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Scheduler
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pass_gens(const BoardDesc &bd, int pass) {
+    const int base = bd.gens / bd.npass, rem = bd.gens - base * bd.npass;
+    return base + (pass <= rem ? 1 : 0);
+}
+
+// Lane 0: wait for queue slot t.  Returns the unit id, or -1 when all work
+// is done or the launch failed (status set).
+static __device__ int wait_for_slot(const PersistArgs &A, int t) {
+    uint64_t t_last = global_ns();
+    int seen = ld_acquire(&A.ctr[2]);
+    unsigned ns = 32;
+    for (long long spin = 0; spin < (1ll << 32); ++spin) {
+        const int v = ld_acquire(&A.ring[t]);
+        if (v >= 0) return v;
+        if (ld_acquire(&A.ctr[3]) != 0) return -1;
+        const int c = ld_acquire(&A.ctr[2]);
+        if (c >= A.total_tasks) return -1;
+        const uint64_t now = global_ns();
+        if (c != seen) {
+            seen = c;
+            t_last = now;
+        } else if (now - t_last > (uint64_t)A.timeout_ns) {
+            atomicCAS(&A.ctr[3], 0, GOL_ETIMEOUT);
+            atomicCAS(A.sticky, 0, GOL_ETIMEOUT);
+            return -1;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+    }
+    atomicCAS(&A.ctr[3], 0, GOL_ETIMEOUT);
+    atomicCAS(A.sticky, 0, GOL_ETIMEOUT);
+    return -1;
+}
+
+__device__ __forceinline__ void enqueue(const PersistArgs &A, int v) {
+    const int slot = atomicAdd(&A.ctr[1], 1);
+    st_release(&A.ring[slot], v);
+}
+
+// Lane 0, after unit u finished pass `pass`: publish it and schedule the
+// units it may have made ready.  Returns the unit this warp runs next or -1.
+static __device__ int complete_pass(const PersistArgs &A, int u, int pass) {
+    const UnitDesc &ud = A.units[u];
+    const BoardDesc &bd = A.boards[ud.board];
+    st_release(&A.done[u], pass);
+    fence_sc_gpu();
+    atomicAdd(&A.ctr[2], 1);
+    const int npass = bd.npass;
+    if (pass == npass) {
+        // last unit of the board to finish flips the board's current buffer
+        if (atomicAdd(&A.ctr[4 + ud.board], 1) == bd.nunits - 1) {
+            if (npass & 1) *bd.cur ^= 1;
+            A.ctr[4 + ud.board] = 0;
+        }
+    }
+    int next = -1;
+    for (int i = -1; i < ud.nnb; ++i) {
+        const int v = i < 0 ? u : ud.nb[i];
+        const int d = ld_acquire(&A.done[v]);
+        if (d >= npass) continue;                       // finished
+        if (ld_acquire(&A.claimed[v]) != d) continue;   // running or queued
+        const UnitDesc &vd = A.units[v];
+        bool ready = true;
+        for (int k = 0; k < vd.nnb; ++k)
+            if (ld_acquire(&A.done[vd.nb[k]]) < d) {
+                ready = false;
+                break;
+            }
+        if (!ready) continue;
+        if (atomicCAS(&A.claimed[v], d, d + 1) != d) continue;
+        if (next < 0)
+            next = v;
+        else
+            enqueue(A, v);
+    }
+    return next;
+}
+
+template <int K, bool TORUS>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+persistent_step_kernel(const PersistArgs A) {
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int u = -1;
+    for (;;) {
+        if (u < 0) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(&A.ctr[0], 1);
+            t = __shfl_sync(kFull, t, 0);
+            if (t >= A.total_tasks) return;
+            int v = -1;
+            if (lane == 0) v = wait_for_slot(A, t);
+            v = __shfl_sync(kFull, v, 0);
+            if (v < 0) return;
+            u = v;
+        }
+        const UnitDesc ud = A.units[u];
+        const BoardDesc bd = A.boards[ud.board];
+        int pass = 0, cur = 0;
+        if (lane == 0) {
+            pass = ld_acquire(&A.done[u]) + 1;
+            cur = ld_acquire(bd.cur);
+        }
+        pass = __shfl_sync(kFull, pass, 0);
+        cur = __shfl_sync(kFull, cur, 0);
+        const uint64_t *src = bd.buf[(cur + pass - 1) & 1];
+        uint64_t *dst = bd.buf[(cur + pass) & 1];
+        run_unit_pass<K, TORUS>(bd, ud, src, dst, pass_gens(bd, pass));
+        __threadfence();
+        __syncwarp();
+        int next = -1;
+        if (lane == 0) next = complete_pass(A, u, pass);
+        u = __shfl_sync(kFull, next, 0);
+    }
+}
+
+template <int K>
+cudaError_t launch_persistent_impl(const PersistArgs &a, bool torus, int grid, cudaStream_t s) {
+    if (torus)
+        persistent_step_kernel<K, true><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+    else
+        persistent_step_kernel<K, false><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t persistent_occupancy_impl(bool torus, int *bps) {
+    if (torus)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true>,
+                                                             kWarpsPerBlock * 32, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false>,
+                                                         kWarpsPerBlock * 32, 0);
+}
+
+#define GOL_INSTANTIATE_PERSISTENT(KV)                                                          \
+    template <>                                                                                 \
+    cudaError_t launch_persistent<KV>(const PersistArgs &a, bool torus, int grid, cudaStream_t s) { \
+        return launch_persistent_impl<KV>(a, torus, grid, s);                                   \
+    }                                                                                           \
+    template <>                                                                                 \
+    cudaError_t persistent_occupancy<KV>(bool torus, int *bps) {                                \
+        return persistent_occupancy_impl<KV>(torus, bps);                                       \
+    }
+
+}  // namespace gol

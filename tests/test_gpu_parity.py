@@ -1,0 +1,303 @@
+"""GPU parity: the CUDA path against the oracle, cell by cell (bit-exact).
+
+Every expected value comes from ``oracle`` on inputs made by ``synth``; the
+CUDA path is reached only through the C ABI (the ctypes binding)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gol():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1209_4408_gb300 as g
+
+    g.gol_set_option(g.GOL_OPT_GENS_PER_PASS, 0)
+    g.gol_set_option(g.GOL_OPT_TILE_ROWS, 0)
+    yield g
+    g.gol_set_option(g.GOL_OPT_GENS_PER_PASS, 0)
+    g.gol_set_option(g.GOL_OPT_TILE_ROWS, 0)
+
+
+@pytest.fixture
+def opts(gol):
+    """Force generations per pass / tile rows, restoring the defaults."""
+    def set_(k=0, rows=0):
+        gol.gol_set_option(gol.GOL_OPT_GENS_PER_PASS, k)
+        gol.gol_set_option(gol.GOL_OPT_TILE_ROWS, rows)
+    yield set_
+    set_(0, 0)
+
+
+def run_gpu(gol, cells, gens, torus=True, layout=0):
+    b = gol.Board(cells.shape[0], cells.shape[1], torus=torus, layout=layout)
+    b.set(cells)
+    b.step(gens)
+    out = b.get()
+    b.close()
+    return out
+
+
+def assert_same(got, want, what):
+    if not np.array_equal(got, want):
+        bad = np.argwhere(got != want)
+        raise AssertionError("%s: %d cells differ, first at %s" % (what, len(bad), bad[:5].tolist()))
+
+
+# ---------------------------------------------------------------------------
+# byte-per-cell path
+# ---------------------------------------------------------------------------
+def test_bytes_256_every_generation(gol):
+    # 256x256 torus, Bernoulli(0.3), 1000 generations, checked after each one
+    R = C = 256
+    cells = synth.bernoulli_board(R, C, 0.3, synth.SEED_BYTES_256)
+    b = gol.Board(R, C, torus=True, layout=gol.GOL_LAYOUT_BYTES)
+    b.set(cells)
+    x = cells
+    for g in range(1, 1001):
+        b.step(1)
+        x = oracle.step(x)
+        assert_same(b.get(), x, "bytes 256x256 generation %d" % g)
+    assert b.generation() == 1000
+    assert b.population() == oracle.population(x)
+
+
+@pytest.mark.parametrize("R,C", [(1, 1), (1, 3), (2, 2), (3, 3), (2, 5), (4, 3)])
+@pytest.mark.parametrize("torus", [True, False])
+def test_bytes_brute_force_tiny(gol, R, C, torus):
+    b = gol.Board(R, C, torus=torus, layout=gol.GOL_LAYOUT_BYTES)
+    for bits in range(1 << (R * C)):
+        cells = np.array([(bits >> i) & 1 for i in range(R * C)], dtype=np.uint8).reshape(R, C)
+        b.set(cells)
+        b.step(1)
+        assert_same(b.get(), oracle.step(cells, torus=torus), "bytes %dx%d state %d" % (R, C, bits))
+
+
+@pytest.mark.parametrize("R,C", [(5, 7), (64, 100), (131, 67)])
+def test_bytes_random_multi_gen(gol, R, C):
+    cells = synth.bernoulli_board(R, C, 0.4, R * C)
+    for torus in (True, False):
+        assert_same(run_gpu(gol, cells, 17, torus, gol.GOL_LAYOUT_BYTES), oracle.run(cells, 17, torus),
+                    "bytes %dx%d" % (R, C))
+
+
+# ---------------------------------------------------------------------------
+# packed path: the rule at every bit position and across both wraps
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("R,C", [(8, 64), (64, 128), (5, 2112)])
+def test_packed_all_512_neighbourhoods(gol, R, C):
+    # each 3x3 neighbourhood on its own board, centred on a bit position in
+    # {0, 1, 31, 32, 62, 63} of some word, on the first/last row and across
+    # the left/right wrap; all boards stepped in one batch
+    W = C // 64
+    positions = []
+    for bit in (0, 1, 31, 32, 62, 63):
+        for word in sorted({0, W - 1, W // 2}):
+            for row in sorted({0, R - 1, R // 2}):
+                positions.append((row, 64 * word + bit))
+    boards, starts = [], []
+    for nb in range(512):
+        pat = np.array([(nb >> i) & 1 for i in range(9)], dtype=np.uint8).reshape(3, 3)
+        r, c = positions[nb % len(positions)]
+        cells = np.zeros((R, C), dtype=np.uint8)
+        for i in range(3):
+            for j in range(3):
+                cells[(r - 1 + i) % R, (c - 1 + j) % C] = pat[i, j]
+        b = gol.Board(R, C, torus=True)
+        b.set(cells)
+        boards.append(b)
+        starts.append(cells)
+    gol.step_batch(boards, [1] * len(boards))
+    for nb, (b, cells) in enumerate(zip(boards, starts)):
+        assert_same(b.get(), oracle.step(cells), "neighbourhood %d on %dx%d" % (nb, R, C))
+        b.close()
+
+
+@pytest.mark.parametrize("torus", [True, False])
+@pytest.mark.parametrize("R,C", [
+    (1, 64), (2, 64), (3, 128), (7, 192), (64, 64), (100, 320), (257, 448), (33, 1024),
+    (64, 1984), (50, 2048), (17, 2112), (40, 2880), (130, 4096), (9, 6400),
+])
+def test_packed_random_shapes(gol, opts, R, C, torus):
+    cells = synth.bernoulli_board(R, C, 0.37, 1000 * R + C)
+    for k, rows in [(1, 0), (4, 3), (8, 0), (16, 64)]:
+        opts(k, rows)
+        for gens in (1, 5, 19):
+            assert_same(run_gpu(gol, cells, gens, torus), oracle.run(cells, gens, torus),
+                        "%dx%d torus=%s K=%d rows=%d gens=%d" % (R, C, torus, k, rows, gens))
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("rows", [1, 8, 64, 1000])
+def test_packed_result_independent_of_pass_and_tile(gol, opts, k, rows):
+    R, C, G = 192, 2240, 23
+    cells = synth.bernoulli_board(R, C, 0.5, 4242)
+    want = oracle.run(cells, G)
+    opts(k, rows)
+    assert_same(run_gpu(gol, cells, G), want, "K=%d rows=%d" % (k, rows))
+
+
+def test_packed_split_runs_compose(gol):
+    cells = synth.bernoulli_board(160, 960, 0.45, 77)
+    b = gol.Board(160, 960)
+    b.set(cells)
+    for g in (3, 0, 8, 1, 13):
+        b.step(g)
+    assert b.generation() == 25
+    assert_same(b.get(), oracle.run(cells, 25), "split run")
+
+
+@pytest.mark.parametrize("N", [64, 128, 1024])
+def test_packed_glider_returns_after_4N(gol, N):
+    cells = synth.pattern_board(N, N, "glider", N - 2, N - 3)
+    b = gol.Board(N, N)
+    b.set(cells)
+    b.step(4 * N)
+    assert_same(b.get(), cells, "glider on %dx%d" % (N, N))
+    b.step(4)
+    assert_same(b.get(), np.roll(cells, (1, 1), axis=(0, 1)), "glider moved")
+
+
+def test_packed_still_lifes_and_blinker(gol):
+    cells = np.zeros((64, 128), np.uint8)
+    synth.place(cells, "block", 10, 62)       # straddles a word boundary
+    synth.place(cells, "beehive", 63, 126)    # straddles both wraps
+    synth.place(cells, "blinker", 30, 30)
+    b = gol.Board(64, 128)
+    b.set(cells)
+    b.step(100)
+    assert_same(b.get(), cells, "period-2 and still objects after 100 generations")
+    b.step(1)
+    assert not np.array_equal(b.get(), cells)
+
+
+def test_closed_forms(gol):
+    for R, C in [(3, 64), (64, 128), (40, 2112)]:
+        assert not run_gpu(gol, np.ones((R, C), np.uint8), 1).any()
+        r, c = np.indices((R + R % 2, C))
+        chk = ((r + c) % 2 == 0).astype(np.uint8)
+        assert not run_gpu(gol, chk, 1).any()
+        assert not run_gpu(gol, np.zeros((R, C), np.uint8), 9).any()
+
+
+def test_batch_equals_alone(gol):
+    specs = synth.batch_specs(24, seed=5, side_hi=700, gen_lo=3, gen_hi=60)
+    boards, cells = [], []
+    for s in specs:
+        c = synth.bernoulli_board(s.rows, s.cols, s.density, s.seed)
+        b = gol.Board(s.rows, s.cols)
+        b.set(c)
+        boards.append(b)
+        cells.append(c)
+    gol.step_batch(boards, [s.gens for s in specs])
+    for s, b, c in zip(specs, boards, cells):
+        got = b.get()
+        assert_same(got, oracle.run(c, s.gens), "batch board %d" % s.index)
+        assert_same(got, run_gpu(gol, c, s.gens), "alone board %d" % s.index)
+        assert b.generation() == s.gens
+
+
+def test_batch_repeat_replays_graph(gol):
+    import torch
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        gol.gol_set_stream(stream)
+        try:
+            specs = synth.batch_specs(12, seed=8, side_hi=400, gen_lo=5, gen_hi=40)
+            boards, cells = [], []
+            for s in specs:
+                c = synth.bernoulli_board(s.rows, s.cols, s.density, s.seed)
+                b = gol.Board(s.rows, s.cols)
+                b.set(c)
+                boards.append(b)
+                cells.append(c)
+            for rep in range(4):          # first call launches, later ones replay a graph
+                gol.step_batch(boards, [s.gens for s in specs])
+            for s, b, c in zip(specs, boards, cells):
+                assert_same(b.get(), oracle.run(c, 4 * s.gens), "graph replay board %d" % s.index)
+        finally:
+            gol.gol_set_stream(None)
+
+
+def test_mixed_layouts_and_edges_in_one_batch(gol):
+    cases = [(50, 64, True, 0), (50, 64, False, 0), (30, 45, True, 0), (30, 45, False, 0), (70, 2176, False, 0)]
+    boards, cells, gens = [], [], []
+    for i, (R, C, t, lay) in enumerate(cases):
+        c = synth.bernoulli_board(R, C, 0.4, 300 + i)
+        b = gol.Board(R, C, torus=t, layout=lay)
+        b.set(c)
+        boards.append(b)
+        cells.append(c)
+        gens.append(7 + i)
+    gol.step_batch(boards, gens)
+    for (R, C, t, _), b, c, g in zip(cases, boards, cells, gens):
+        assert_same(b.get(), oracle.run(c, g, t), "mixed %dx%d torus=%s" % (R, C, t))
+
+
+def test_population_region_and_packed_io(gol):
+    R, C = 96, 640
+    cells = synth.bernoulli_board(R, C, 0.3, 11)
+    b = gol.Board(R, C)
+    b.set(cells)
+    b.step(6)
+    want = oracle.run(cells, 6)
+    assert b.population() == oracle.population(want)
+    reg = b.region(90, 600, 20, 70)               # straddles both wraps
+    assert_same(reg, want[np.ix_(np.arange(90, 110) % R, np.arange(600, 670) % C)], "region")
+    assert_same(oracle.unpack_words(b.get_packed()), want, "packed read")
+    b2 = gol.Board(R, C)
+    b2.set_packed(synth.pack_cells(want))
+    assert_same(b2.get(), want, "packed write")
+
+
+def test_torch_allocator_and_stream(gol):
+    import torch
+
+    stream = gol.use_torch_allocator()
+    try:
+        cells = synth.bernoulli_board(128, 256, 0.5, 3)
+        assert_same(run_gpu(gol, cells, 12), oracle.run(cells, 12), "torch allocator")
+        dev = torch.empty(128 * 4, dtype=torch.int64, device="cuda")
+        b = gol.Board(128, 256)
+        b.set(cells)
+        b.step(3)
+        gol.gol_get_packed_device(b.handle, dev.data_ptr(), dev.numel())
+        stream.synchronize()
+        got = dev.cpu().numpy().view(np.uint64).reshape(128, 4)
+        assert_same(oracle.unpack_words(got), oracle.run(cells, 3), "device read")
+    finally:
+        gol.gol_set_allocator(None, None)
+        gol.gol_set_stream(None)
+
+
+def test_invalid_arguments(gol):
+    with pytest.raises(gol.GolError) as e:
+        gol.gol_create_ex(64, 100, True, gol.GOL_LAYOUT_PACKED)
+    assert e.value.code == gol.GOL_EINVAL
+    b = gol.Board(8, 64)
+    bad = np.zeros((8, 64), np.uint8)
+    bad[3, 5] = 2
+    with pytest.raises(gol.GolError):
+        b.set(bad)
+    with pytest.raises(gol.GolError):
+        b.step(-1)
+    with pytest.raises(gol.GolError):
+        gol.gol_step_batch([b.handle, b.handle], [1, 1])
+    with pytest.raises(gol.GolError):
+        gol.gol_set(b.handle, np.zeros(10, np.uint8))
+    for rows, cols in [(0, 64), (64, 0), (-1, 5)]:
+        with pytest.raises(gol.GolError):
+            gol.gol_create(rows, cols, True)
+
+
+def test_bounded_wait_times_out_and_context_survives(gol):
+    assert gol.gol_debug_unfilled_wait(200) == gol.GOL_ETIMEOUT
+    cells = synth.bernoulli_board(64, 128, 0.5, 1)
+    assert_same(run_gpu(gol, cells, 9), oracle.run(cells, 9), "after timeout")
