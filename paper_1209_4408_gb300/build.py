@@ -2,8 +2,9 @@
 
 Each translation unit under csrc/ is compiled by nvcc in parallel, then the
 objects are linked into ``paper_1209_4408_gb300/libgol.so``.  Rebuilds only
-when a source or header is newer than the library.  Run directly
-(``python -m paper_1209_4408_gb300.build``) or through ``__graft_entry__.build()``.
+when a source or header is newer than the library.  Run it as a script
+(``python paper_1209_4408_gb300/build.py``) or through
+``__graft_entry__.build()``; importing the package needs the library built.
 """
 from __future__ import annotations
 

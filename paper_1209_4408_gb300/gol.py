@@ -65,7 +65,7 @@ def load() -> ctypes.CDLL:
         return _lib
     if not os.path.exists(LIB_PATH):
         raise ImportError("libgol.so is missing (%s); build it with "
-                          "`python -m paper_1209_4408_gb300.build` or __graft_entry__.build()" % LIB_PATH)
+                          "`python paper_1209_4408_gb300/build.py` or __graft_entry__.build()" % LIB_PATH)
     lib = ctypes.CDLL(LIB_PATH)
     i64, i32, vp, sz = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
     P = ctypes.POINTER
