@@ -225,15 +225,16 @@ def gol_set_stream(stream) -> None:
     _check(load().gol_set_stream(ptr))
 
 
-_alloc_refs = None
+# Callback objects handed to the library stay alive for the life of the
+# process: boards keep the allocator they were created with and call its free
+# function when destroyed, possibly after the process-wide hook has changed.
+_alloc_keep: list = []
 
 
 def gol_set_allocator(alloc_fn, free_fn, ctx=None):
     """alloc_fn(size) -> int device pointer, free_fn(ptr); both None restores cudaMalloc."""
-    global _alloc_refs
     if alloc_fn is None and free_fn is None:
         _check(load().gol_set_allocator(ALLOC_FN(), FREE_FN(), None))
-        _alloc_refs = None
         return
 
     def _a(size, _ctx):
@@ -246,8 +247,8 @@ def gol_set_allocator(alloc_fn, free_fn, ctx=None):
         free_fn(ptr)
 
     refs = (ALLOC_FN(_a), FREE_FN(_f))
+    _alloc_keep.append(refs)
     _check(load().gol_set_allocator(refs[0], refs[1], None))
-    _alloc_refs = refs
 
 
 def use_torch_allocator(device: int | None = None):
