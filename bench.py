@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--plain-sample", type=int, default=64, help="boards timed in the plain loop")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-probe", action="store_true", help="skip the integer-throughput probe")
     return ap.parse_args()
 
 
@@ -296,7 +298,7 @@ def run_gpu(args, rank, world, local):
                "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps}
 
     # ---- roofline of the dominant kernel (the persistent step kernel) ---------------
-    ops, _ = gol.gol_probe_int_throughput()
+    ops = float("nan") if args.no_probe else gol.gol_probe_int_throughput()[0]
     achieved_tops = total_words_gens * INT_OPS_PER_WORD_GEN / (min(step_ms) * 1e-3) / 1e12 \
         if layout == gol.GOL_LAYOUT_PACKED else None
     roofline = None
@@ -328,10 +330,14 @@ def run_gpu(args, rank, world, local):
         out["e2e"] = e2e
     if roofline:
         out["roofline"] = roofline
+    for b in boards:
+        b.close()
+    gol.gol_set_allocator(None, None)
     if rank == 0:
-        g, cores, desc = cpu_oracle_sample(specs, args.cpu_seconds, 1)
-        out["cpu_baseline"] = {"value": round(g, 5), "unit": "GCUPS", "cores": cores, "kind": "oracle",
-                               "sample": desc}
+        if not args.no_cpu:
+            g, cores, desc = cpu_oracle_sample(specs, args.cpu_seconds, 1)
+            out["cpu_baseline"] = {"value": round(g, 5), "unit": "GCUPS", "cores": cores, "kind": "oracle",
+                                   "sample": desc}
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

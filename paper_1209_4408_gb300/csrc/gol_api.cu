@@ -368,13 +368,16 @@ cudaError_t launch_plan_kernels(const Plan &P, cudaStream_t s) {
 
 // plan cache (most recently used first); evicted plans wait in the
 // graveyard until the work queued before their eviction has finished
-std::vector<std::unique_ptr<Plan>> g_plans;
+// Both lists live on the heap and are never destroyed: at process exit the
+// allocator hook (e.g. a Python callback) may already be gone, so no plan
+// memory is released from a static destructor.
+std::vector<std::unique_ptr<Plan>> &g_plans = *new std::vector<std::unique_ptr<Plan>>();
 constexpr size_t kMaxPlans = 16;
 struct Grave {
     std::unique_ptr<Plan> plan;
     cudaEvent_t ev;
 };
-std::vector<Grave> g_graves;
+std::vector<Grave> &g_graves = *new std::vector<Grave>();
 
 void bury(std::unique_ptr<Plan> p) {
     cudaEvent_t ev = nullptr;

@@ -11,8 +11,10 @@ library's device allocations through the PyTorch caching allocator and
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 from typing import Iterable, Sequence
 
 import numpy as np
@@ -314,8 +316,10 @@ class Board:
     """Owning wrapper of a gol_handle."""
 
     def __init__(self, rows: int, cols: int, torus: bool = True, layout: int = GOL_LAYOUT_AUTO):
+        self.handle = None
         self.handle = gol_create_ex(rows, cols, torus, layout)
         self.rows, self.cols, self.torus, self.layout = gol_info(self.handle)
+        _live_boards.add(self)
 
     @property
     def packed(self) -> bool:
@@ -365,3 +369,22 @@ class Board:
 
 def step_batch(boards: Sequence[Board], generations: Iterable[int]):
     gol_step_batch([b.handle for b in boards], generations)
+
+
+_live_boards: "weakref.WeakSet[Board]" = weakref.WeakSet()
+
+
+@atexit.register
+def _release_at_exit():
+    """Frees boards and cached plans while Python callbacks still work."""
+    if _lib is None:
+        return
+    for b in list(_live_boards):
+        try:
+            b.close()
+        except Exception:
+            pass
+    try:
+        gol_set_allocator(None, None)
+    except Exception:
+        pass

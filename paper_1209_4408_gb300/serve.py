@@ -78,7 +78,8 @@ class ServeStats:
 class Server:
     def __init__(self, budget_bytes: int = 120 << 30, tick_target_s: float = 0.02,
                  quantum_min: int = 8, quantum_max: int = 1 << 16, keep_results: bool = False,
-                 clock: Callable[[], float] = time.perf_counter):
+                 clock: Callable[[], float] = time.perf_counter, backend=None):
+        self.g = backend if backend is not None else gol
         self.budget = budget_bytes
         self.tick_target = tick_target_s
         self.qmin, self.qmax = quantum_min, quantum_max
@@ -88,17 +89,17 @@ class Server:
         self.rate_cups = None             # measured cell updates per second
 
     def _admit(self, job: Job, now: float):
-        job.handle = gol.gol_create_ex(job.rows, job.cols, True, gol.GOL_LAYOUT_PACKED)
-        gol.gol_set_packed(job.handle, job.words)
+        job.handle = self.g.gol_create_ex(job.rows, job.cols, True, gol.GOL_LAYOUT_PACKED)
+        self.g.gol_set_packed(job.handle, job.words)
         job.remaining = job.gens
         job.admitted_s = now
 
     def _retire(self, job: Job, now: float, stats: ServeStats):
         if self.keep:
-            job.result = gol.gol_get_packed(job.handle)
+            job.result = self.g.gol_get_packed(job.handle)
         else:
-            gol.gol_sync(job.handle)
-        gol.gol_destroy(job.handle)
+            self.g.gol_sync(job.handle)
+        self.g.gol_destroy(job.handle)
         job.handle = None
         job.done_s = now
         stats.latencies_s.append(now - job.arrival_s)
@@ -136,13 +137,13 @@ class Server:
             q = [min(j.remaining, self.quantum) for j in active]
             cells_gens = sum(j.rows * j.cols * g for j, g in zip(active, q))
             t_tick = self.clock()
-            gol.gol_step_batch([j.handle for j in active], q)
+            self.g.gol_step_batch([j.handle for j in active], q)
             # admit arrivals while the tick runs (uploads queue behind it)
             now = self.clock() - t0
             while nxt < len(jobs) and jobs[nxt].arrival_s <= now:
                 waiting.append(jobs[nxt])
                 nxt += 1
-            gol.gol_sync(active[0].handle)
+            self.g.gol_sync(active[0].handle)
             dt = self.clock() - t_tick
             stats.ticks += 1
             stats.cell_updates += cells_gens

@@ -1,0 +1,116 @@
+"""Continuous-batching server: host logic on CPU (fake backend) and, on the
+GPU, every result equal alone and in the mix."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+@pytest.fixture(scope="module")
+def serve_mod():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1209_4408_gb300 import serve
+
+    return serve
+
+
+class FakeBackend:
+    """Records calls; a board is a dict with its remaining generations."""
+
+    def __init__(self):
+        self.ids = itertools.count(1)
+        self.boards = {}
+        self.live_bytes = 0
+        self.peak = 0
+        self.batches = []
+
+    def gol_create_ex(self, rows, cols, torus, layout):
+        h = next(self.ids)
+        self.boards[h] = {"rows": rows, "cols": cols, "gen": 0}
+        self.live_bytes += 2 * rows * cols // 8
+        self.peak = max(self.peak, self.live_bytes)
+        return h
+
+    def gol_set_packed(self, h, words):
+        assert words.shape == (self.boards[h]["rows"], self.boards[h]["cols"] // 64)
+
+    def gol_step_batch(self, hs, gens):
+        assert len(set(hs)) == len(hs)
+        self.batches.append(list(zip(hs, gens)))
+        for h, g in zip(hs, gens):
+            assert g > 0
+            self.boards[h]["gen"] += g
+
+    def gol_sync(self, h):
+        pass
+
+    def gol_get_packed(self, h):
+        return self.boards[h]["gen"]
+
+    def gol_destroy(self, h):
+        b = self.boards.pop(h)
+        self.live_bytes -= 2 * b["rows"] * b["cols"] // 8
+
+
+def make_jobs(serve, n, rate, seed=3, side_hi=512, gen_hi=300):
+    reqs = synth.request_stream(n, rate, seed=seed, side_hi=side_hi, gen_lo=5, gen_hi=gen_hi)
+    return [serve.Job(r.index, r.arrival_s, r.rows, r.cols, r.gens,
+                      synth.bernoulli_words(r.rows, r.cols, r.density, r.seed)) for r in reqs]
+
+
+def test_host_logic_budget_fifo_and_generations(serve_mod):
+    fake = FakeBackend()
+    jobs = make_jobs(serve_mod, 40, rate=1e6)                  # all arrive at once
+    budget = 3 * max(j.bytes_on_device for j in jobs)
+    srv = serve_mod.Server(budget_bytes=budget, tick_target_s=1e-4, keep_results=True, backend=fake)
+    st = srv.run(jobs)
+    assert st.summary()["requests"] == len(jobs)
+    assert fake.peak <= budget                                  # admission respects the budget
+    assert all(j.result == j.gens for j in jobs)                # every board got exactly its generations
+    assert not fake.boards                                      # everything freed
+    admitted = sorted(jobs, key=lambda j: j.admitted_s)
+    assert [j.rid for j in admitted] == sorted(j.rid for j in jobs)   # FIFO admission
+    assert st.max_waiting > 0 and st.ticks > 1
+
+
+def test_host_logic_rejects_oversized_request(serve_mod):
+    fake = FakeBackend()
+    jobs = make_jobs(serve_mod, 3, rate=1e6)
+    srv = serve_mod.Server(budget_bytes=16, backend=fake)
+    with pytest.raises(RuntimeError):
+        srv.run(jobs)
+
+
+@pytest.mark.gpu
+def test_served_results_equal_alone_and_oracle(serve_mod):
+    from paper_1209_4408_gb300 import gol
+
+    jobs = make_jobs(serve_mod, 24, rate=2000.0)
+    srv = serve_mod.Server(budget_bytes=1 << 24, tick_target_s=0.002, keep_results=True)
+    st = srv.run(jobs)
+    assert st.summary()["requests"] == len(jobs)
+    assert st.ticks > 1 and st.max_active > 1                  # boards really shared launches
+    for j in jobs:
+        h = gol.gol_create_ex(j.rows, j.cols, True, gol.GOL_LAYOUT_PACKED)
+        gol.gol_set_packed(h, j.words)
+        gol.gol_step(h, j.gens)
+        alone = gol.gol_get_packed(h)
+        gol.gol_destroy(h)
+        assert np.array_equal(j.result, alone), "request %d differs alone and in the mix" % j.rid
+        want = oracle.run(oracle.unpack_words(j.words), j.gens)
+        assert np.array_equal(oracle.unpack_words(j.result), want), "request %d vs oracle" % j.rid
+
+
+@pytest.mark.gpu
+def test_fcfs_baseline_matches(serve_mod):
+    jobs = make_jobs(serve_mod, 8, rate=5000.0, seed=4)
+    st = serve_mod.serve_fcfs(jobs, keep_results=True)
+    assert st.summary()["requests"] == 8
+    for j in jobs:
+        want = oracle.run(oracle.unpack_words(j.words), j.gens)
+        assert np.array_equal(oracle.unpack_words(j.result), want)
