@@ -135,9 +135,11 @@ const char *gol_last_error(void);
 
 /* Tuning knobs (process wide).  Keys:
  *   GOL_OPT_GENS_PER_PASS  generations per pass over a packed board (1, 2,
- *                          4, 8 or 16; 0 = let the autotune table decide)
+ *                          3, 4, 5, 6, 8 or 16; 0 = let the autotune table
+ *                          decide)
  *   GOL_OPT_TILE_ROWS      rows per warp strip of a packed board (>= 1;
- *                          0 = autotune table)
+ *                          0 = autotune table, shortened for boards with
+ *                          many passes so that no chain of passes dominates)
  *   GOL_OPT_USE_GRAPHS     1 = capture/replay gol_step_batch in CUDA graphs
  *   GOL_OPT_WAIT_TIMEOUT_MS  limit of the device-side bounded waits
  *                          (default 5000 ms without progress)

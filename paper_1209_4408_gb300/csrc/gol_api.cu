@@ -175,7 +175,7 @@ std::pair<int, int> size_class(int64_t rows, int64_t cols) {
 }
 TuneEntry tune_lookup(int64_t rows, int64_t cols) {
     auto it = g_tune.find(size_class(rows, cols));
-    TuneEntry t{8, 64};
+    TuneEntry t{4, 32};
     if (it != g_tune.end()) t = it->second;
     if (g_opt_k) t.k = (int)g_opt_k;
     if (g_opt_rows) t.rows = (int)g_opt_rows;
@@ -213,10 +213,38 @@ struct Plan {
     }
 };
 
+// generations-per-pass values with a kernel instantiation (persist_k*.cu)
+#define GOL_FOR_EACH_K(X) X(1) X(2) X(3) X(4) X(5) X(6) X(8) X(16)
+constexpr int kKs[] = {1, 2, 3, 4, 5, 6, 8, 16};
+
+bool is_supported_k(int k) {
+    for (int v : kKs)
+        if (v == k) return true;
+    return false;
+}
 int supported_k(int k) {
     int s = 1;
-    while (s * 2 <= k && s < 16) s *= 2;
+    for (int v : kKs)
+        if (v <= k) s = v;
     return s;
+}
+cudaError_t occupancy_for(int K, bool torus, int *bps) {
+    switch (K) {
+#define X(KV) \
+    case KV: return persistent_occupancy<KV>(torus, bps);
+        GOL_FOR_EACH_K(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+}
+cudaError_t launch_for(int K, const PersistArgs &a, bool torus, int grid, cudaStream_t s) {
+    switch (K) {
+#define X(KV) \
+    case KV: return launch_persistent<KV>(a, torus, grid, s);
+        GOL_FOR_EACH_K(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
 }
 
 // split rows [0, R) into nb balanced blocks; block i = [R*i/nb, R*(i+1)/nb)
@@ -291,6 +319,34 @@ int build_plan(Plan &P) {
         }
     }
     P.K = supported_k(std::max(1, K));
+    int bps = 1;
+    cudaError_t e = occupancy_for(P.K, P.torus, &bps);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    const int64_t slots = (int64_t)g_dev.sms * std::max(1, bps) * kWarpsPerBlock;
+    // Tile rows per board.  The tune table gives the tallest (most efficient)
+    // unit; a board with many passes gets shorter units when its chain of
+    // passes, npass * (H + 2K) row iterations, would exceed half of the
+    // average work per warp slot, so that long runs do not set the makespan.
+    std::vector<int> hrows(n);
+    double work = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const gol_board *h = P.hs[i];
+        const int64_t np = (P.gens[i] + P.K - 1) / P.K;
+        hrows[i] = std::max(1, tune_lookup(h->rows, h->cols).rows);
+        const int W = (int)h->words;
+        const int S = W <= 32 ? std::max(1, 32 / W) : 1;
+        const int nt = W <= 32 ? 1 : (W + kTileWords - 1) / kTileWords;
+        const double units = std::ceil((double)h->rows / ((double)S * hrows[i])) * nt;
+        work += units * np * (double)(hrows[i] + 2 * P.K);
+    }
+    const double chain_cap = g_opt_rows ? 1e300 : 0.5 * work / (double)slots;
+    for (size_t i = 0; i < n; ++i) {
+        const int64_t np = (P.gens[i] + P.K - 1) / P.K;
+        if ((double)np * (hrows[i] + 2 * P.K) > chain_cap) {
+            const int h = (int)(chain_cap / (double)np) - 2 * P.K;
+            hrows[i] = std::max(std::max(8, P.K), std::min(hrows[i], h));
+        }
+    }
     P.total_tasks = 0;
     for (size_t i = 0; i < n; ++i) {
         gol_board *h = P.hs[i];
@@ -302,8 +358,7 @@ int build_plan(Plan &P) {
         bd.W = (int32_t)h->words;
         bd.gens = (int32_t)P.gens[i];
         bd.npass = (int32_t)((P.gens[i] + P.K - 1) / P.K);
-        const TuneEntry te = tune_lookup(h->rows, h->cols);
-        build_units(h, (int)i, P.K, te.rows, P.units, &bd.nunits);
+        build_units(h, (int)i, P.K, hrows[i], P.units, &bd.nunits);
         P.total_tasks += (int64_t)bd.nunits * bd.npass;
         P.boards.push_back(bd);
         P.npass.push_back(bd.npass);
@@ -338,16 +393,6 @@ int build_plan(Plan &P) {
     a.nunits = (int32_t)nu;
     a.total_tasks = (int32_t)P.total_tasks;
     a.timeout_ns = g_opt_timeout_ms * 1000000ll;
-    int bps = 1;
-    cudaError_t e = cudaSuccess;
-    switch (P.K) {
-        case 1: e = persistent_occupancy<1>(P.torus, &bps); break;
-        case 2: e = persistent_occupancy<2>(P.torus, &bps); break;
-        case 4: e = persistent_occupancy<4>(P.torus, &bps); break;
-        case 8: e = persistent_occupancy<8>(P.torus, &bps); break;
-        default: e = persistent_occupancy<16>(P.torus, &bps); break;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     const int64_t max_blocks = (int64_t)g_dev.sms * std::max(1, bps);
     const int64_t want = (int64_t)(nu + kWarpsPerBlock - 1) / kWarpsPerBlock;
     P.grid = (int)std::max<int64_t>(1, std::min(max_blocks, want));
@@ -357,13 +402,7 @@ int build_plan(Plan &P) {
 cudaError_t launch_plan_kernels(const Plan &P, cudaStream_t s) {
     cudaError_t e = launch_sched_init(P.args, (int)P.boards.size(), s);
     if (e != cudaSuccess) return e;
-    switch (P.K) {
-        case 1: return launch_persistent<1>(P.args, P.torus, P.grid, s);
-        case 2: return launch_persistent<2>(P.args, P.torus, P.grid, s);
-        case 4: return launch_persistent<4>(P.args, P.torus, P.grid, s);
-        case 8: return launch_persistent<8>(P.args, P.torus, P.grid, s);
-        default: return launch_persistent<16>(P.args, P.torus, P.grid, s);
-    }
+    return launch_for(P.K, P.args, P.torus, P.grid, s);
 }
 
 // plan cache (most recently used first); evicted plans wait in the
@@ -813,8 +852,8 @@ int gol_set_option(int key, int64_t v) {
     std::lock_guard<std::mutex> lk(g_mu);
     switch (key) {
         case GOL_OPT_GENS_PER_PASS:
-            if (!(v == 0 || v == 1 || v == 2 || v == 4 || v == 8 || v == 16))
-                return fail(GOL_EINVAL, "generations per pass must be 0, 1, 2, 4, 8 or 16");
+            if (!(v == 0 || is_supported_k((int)v)))
+                return fail(GOL_EINVAL, "generations per pass must be 0 or one of 1, 2, 3, 4, 5, 6, 8, 16");
             g_opt_k = v;
             return GOL_OK;
         case GOL_OPT_TILE_ROWS:
@@ -845,7 +884,7 @@ int gol_get_option(int key, int64_t *v) {
 
 int gol_tune_set(int64_t rows, int64_t cols, int k, int tile_rows) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (rows < 1 || cols < 1 || k < 1 || k > 16 || (k & (k - 1)) || tile_rows < 1)
+    if (rows < 1 || cols < 1 || !is_supported_k(k) || tile_rows < 1)
         return fail(GOL_EINVAL, "bad tune entry");
     g_tune[size_class(rows, cols)] = TuneEntry{k, tile_rows};
     clear_plans();

@@ -103,12 +103,12 @@ __device__ __forceinline__ void st_u64(uint64_t *p, uint32_t lo, uint32_t hi) {
 // ---------------------------------------------------------------------------
 // One pass of one unit by one warp.
 // ---------------------------------------------------------------------------
-template <int K, bool TORUS>
+template <int K, bool TORUS, bool PARTIAL>
 __device__ __forceinline__ void run_unit_pass(const BoardDesc &bd, const UnitDesc &ud,
                                               const uint64_t *__restrict__ src,
                                               uint64_t *__restrict__ dst, int kk) {
     constexpr unsigned kFull = 0xffffffffu;
-    constexpr int PF = (2 * K) % 4 == 0 ? 4 : 2;   // rows prefetched ahead
+    constexpr int PF = 2;                          // rows prefetched ahead (2K is a multiple)
     constexpr int NPRO = 2 * K;                    // prologue iterations
     const int lane = threadIdx.x & 31;
     const int R = bd.R, W = bd.W;
@@ -214,7 +214,7 @@ __device__ __forceinline__ void run_unit_pass(const BoardDesc &bd, const UnitDes
             if (!GUARD || j >= 2 * g + 2) {
                 ol = rule32(p0l[g], p1l[g], c0l[g], c1l[g], n0l, n1l, cal[g]);
                 oh = rule32(p0h[g], p1h[g], c0h[g], c1h[g], n0h, n1h, cah[g]);
-                if (g >= kk) {                              // pass shorter than K: identity stage
+                if (PARTIAL && g >= kk) {                   // pass shorter than K: identity stage
                     ol = cal[g];
                     oh = cah[g];
                 }
@@ -306,42 +306,64 @@ __device__ __forceinline__ void enqueue(const PersistArgs &A, int v) {
     st_release(&A.ring[slot], v);
 }
 
-// Lane 0, after unit u finished pass `pass`: publish it and schedule the
-// units it may have made ready.  Returns the unit this warp runs next or -1.
-static __device__ int complete_pass(const PersistArgs &A, int u, int pass) {
-    const UnitDesc &ud = A.units[u];
-    const BoardDesc &bd = A.boards[ud.board];
-    st_release(&A.done[u], pass);
-    fence_sc_gpu();
-    atomicAdd(&A.ctr[2], 1);
+__device__ __forceinline__ int ld_relaxed(const int32_t *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void red_add(int32_t *p, int v) {
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Whole warp, after unit u finished pass `pass`: publish it and schedule the
+// units it may have made ready.  Lane i examines candidate i (u itself, then
+// its neighbours), so the loads of all candidates overlap.  Returns the unit
+// this warp runs next (u first if it is ready) or -1.
+__device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pass, const UnitDesc &ud,
+                                             const BoardDesc &bd) {
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int npass = bd.npass;
-    if (pass == npass) {
-        // last unit of the board to finish flips the board's current buffer
-        if (atomicAdd(&A.ctr[4 + ud.board], 1) == bd.nunits - 1) {
-            if (npass & 1) *bd.cur ^= 1;
-            A.ctr[4 + ud.board] = 0;
+    if (lane == 0) {
+        st_release(&A.done[u], pass);
+        red_add(&A.ctr[2], 1);
+        if (pass == npass) {
+            // last unit of the board to finish flips the board's current buffer
+            if (atomicAdd(&A.ctr[4 + ud.board], 1) == bd.nunits - 1) {
+                if (npass & 1) *bd.cur ^= 1;
+                A.ctr[4 + ud.board] = 0;
+            }
         }
     }
-    int next = -1;
-    for (int i = -1; i < ud.nnb; ++i) {
-        const int v = i < 0 ? u : ud.nb[i];
-        const int d = ld_acquire(&A.done[v]);
-        if (d >= npass) continue;                       // finished
-        if (ld_acquire(&A.claimed[v]) != d) continue;   // running or queued
-        const UnitDesc &vd = A.units[v];
-        bool ready = true;
-        for (int k = 0; k < vd.nnb; ++k)
-            if (ld_acquire(&A.done[vd.nb[k]]) < d) {
-                ready = false;
-                break;
-            }
-        if (!ready) continue;
-        if (atomicCAS(&A.claimed[v], d, d + 1) != d) continue;
-        if (next < 0)
-            next = v;
-        else
-            enqueue(A, v);
+    __syncwarp();
+    // Every completer orders its `done` store before its reads of the other
+    // counters with a sequentially consistent fence: of two units finishing at
+    // the same time, at least one sees the other's store.
+    fence_sc_gpu();
+    int v = -1, d = 0;
+    bool ready = false;
+    if (lane <= ud.nnb) {
+        v = lane == 0 ? u : A.units[u].nb[lane - 1];
+        d = ld_relaxed(&A.done[v]);
+        const int cl = ld_relaxed(&A.claimed[v]);
+        if (d < npass && cl == d) {
+            const UnitDesc &vd = A.units[v];
+            const int m = vd.nnb;
+            int lo = d;
+#pragma unroll
+            for (int k = 0; k < kMaxNeighbours; ++k)
+                if (k < m) lo = min(lo, ld_relaxed(&A.done[vd.nb[k]]));
+            ready = lo >= d;
+        }
     }
+    fence_acq_rel_gpu();
+    if (ready) ready = atomicCAS(&A.claimed[v], d, d + 1) == d;
+    const unsigned mask = __ballot_sync(kFull, ready);
+    if (!mask) return -1;
+    const int leader = __ffs(mask) - 1;
+    const int next = __shfl_sync(kFull, v, leader);
+    if (ready && lane != leader) enqueue(A, v);
     return next;
 }
 
@@ -374,12 +396,14 @@ persistent_step_kernel(const PersistArgs A) {
         cur = __shfl_sync(kFull, cur, 0);
         const uint64_t *src = bd.buf[(cur + pass - 1) & 1];
         uint64_t *dst = bd.buf[(cur + pass) & 1];
-        run_unit_pass<K, TORUS>(bd, ud, src, dst, pass_gens(bd, pass));
+        const int kk = pass_gens(bd, pass);
+        if (kk == K)
+            run_unit_pass<K, TORUS, false>(bd, ud, src, dst, K);
+        else
+            run_unit_pass<K, TORUS, true>(bd, ud, src, dst, kk);
         __threadfence();
         __syncwarp();
-        int next = -1;
-        if (lane == 0) next = complete_pass(A, u, pass);
-        u = __shfl_sync(kFull, next, 0);
+        u = complete_pass(A, u, pass, ud, bd);
     }
 }
 
