@@ -264,26 +264,18 @@ def run_gpu(args, rank, world, local):
     if not args.no_e2e:
         e2e_steps = max(1, min(args.steps, 3))
         out_pinned = torch.empty_like(pinned) if pinned is not None else None
-        outs = []
-        if out_pinned is not None:
-            host_out = out_pinned.numpy().view(np.uint64)
-            off = 0
-            for s in specs:
-                n = s.rows * s.cols // 64
-                outs.append(host_out[off:off + n].reshape(s.rows, s.cols // 64))
-                off += n
+        host_out = out_pinned.numpy().view(np.uint64) if out_pinned is not None else None
         barrier()
         t0 = time.perf_counter()
         h2d = d2h = 0
         for _ in range(e2e_steps):
             if layout == gol.GOL_LAYOUT_PACKED:
-                for b, v in zip(boards, views):
-                    gol.gol_set_packed(b.handle, v)
-                    h2d += v.nbytes
+                # one upload of all boards, the step, one download of all boards
+                gol.gol_set_packed_batch(handles, host)
+                h2d += host.nbytes
                 step()
-                for b, o in zip(boards, outs):
-                    gol.gol_get_packed(b.handle, o)
-                    d2h += o.nbytes
+                gol.gol_get_packed_batch(handles, host_out)
+                d2h += host_out.nbytes
             else:
                 cells = [synth.bernoulli_board(s.rows, s.cols, s.density, s.seed) for s in specs]
                 for b, c in zip(boards, cells):

@@ -85,6 +85,17 @@ int gol_get_packed(gol_handle h, uint64_t *words, size_t nwords);
 int gol_set_packed_device(gol_handle h, const uint64_t *dwords, size_t nwords);
 int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords);
 
+/* Many packed boards in one transfer.  `words` is host memory holding the
+ * boards hs[0..n) one after the other, board i taking rows*cols/64 words in
+ * the packed layout; nwords must equal the sum.  gol_set_packed_batch copies
+ * the whole buffer to the device at once and scatters it into the boards
+ * (handles must be distinct; generation counters reset to 0; asynchronous
+ * when `words` is pinned).  gol_get_packed_batch gathers the boards'
+ * current states into one device buffer, copies it to `words` and
+ * synchronises.  Non-packed boards are GOL_EINVAL. */
+int gol_set_packed_batch(const gol_handle *hs, size_t n, const uint64_t *words, size_t nwords);
+int gol_get_packed_batch(const gol_handle *hs, size_t n, uint64_t *words, size_t nwords);
+
 /* Copies the nr x nc window whose top-left cell is (r0, c0) to host `out`
  * (nr*nc bytes, row major).  Window indices are taken modulo the board
  * size, so windows may straddle the wrap.  nr, nc >= 0. */

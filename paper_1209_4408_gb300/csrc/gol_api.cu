@@ -175,7 +175,7 @@ std::pair<int, int> size_class(int64_t rows, int64_t cols) {
 }
 TuneEntry tune_lookup(int64_t rows, int64_t cols) {
     auto it = g_tune.find(size_class(rows, cols));
-    TuneEntry t{4, 32};
+    TuneEntry t{6, 32};
     if (it != g_tune.end()) t = it->second;
     if (g_opt_k) t.k = (int)g_opt_k;
     if (g_opt_rows) t.rows = (int)g_opt_rows;
@@ -738,6 +738,69 @@ int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords) {
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
     CU(cudaMemcpyAsync(dwords, h->buf[h->cur], nwords * 8, cudaMemcpyDeviceToDevice, g_stream));
     return GOL_OK;
+}
+
+namespace {
+// shared checks of the many-board transfers; fills descriptors and offsets
+int many_plan(const gol_handle *hs, size_t n, size_t nwords, std::vector<CopyDesc> &d, bool scatter) {
+    if (!hs) return fail(GOL_EINVAL, "null handle array");
+    if (n > (size_t)(1 << 30)) return fail(GOL_EINVAL, "too many boards");
+    std::unordered_set<gol_handle> seen;
+    int64_t off = 0;
+    d.resize(n);
+    for (size_t i = 0; i < n; ++i) {
+        gol_handle h = hs[i];
+        if (!valid(h)) return fail(GOL_EINVAL, "invalid handle at %zu", i);
+        if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board %zu is not packed", i);
+        if (scatter && !seen.insert(h).second) return fail(GOL_EINVAL, "handle repeated at %zu", i);
+        const int64_t nw = h->rows * h->words;
+        d[i].board = (uint64_t *)(scatter ? h->buf[0] : h->buf[h->cur]);
+        d[i].cur = scatter ? h->dev_cur : nullptr;
+        d[i].offset = off;
+        d[i].nwords = nw;
+        off += nw;
+    }
+    if ((size_t)off != nwords) return fail(GOL_EINVAL, "nwords = %zu, the boards hold %lld words", nwords, (long long)off);
+    return GOL_OK;
+}
+}  // namespace
+
+int gol_set_packed_batch(const gol_handle *hs, size_t n, const uint64_t *words, size_t nwords) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (n == 0) return GOL_OK;
+    if (!words) return fail(GOL_EINVAL, "null words");
+    std::vector<CopyDesc> d;
+    int rc = many_plan(hs, n, nwords, d, true);
+    if (rc) return rc;
+    const size_t dbytes = (n * sizeof(CopyDesc) + 255) & ~size_t(255);
+    Scratch st(dbytes + nwords * 8);
+    if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", nwords * 8);
+    CU(cudaMemcpyAsync(st.p, d.data(), n * sizeof(CopyDesc), cudaMemcpyHostToDevice, g_stream));
+    uint64_t *stage = (uint64_t *)((char *)st.p + dbytes);
+    CU(cudaMemcpyAsync(stage, words, nwords * 8, cudaMemcpyHostToDevice, g_stream));
+    CU(launch_scatter_boards((const CopyDesc *)st.p, (int)n, stage, g_stream));
+    for (size_t i = 0; i < n; ++i) {
+        hs[i]->cur = 0;
+        hs[i]->generation = 0;
+    }
+    return GOL_OK;
+}
+
+int gol_get_packed_batch(const gol_handle *hs, size_t n, uint64_t *words, size_t nwords) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (n == 0) return GOL_OK;
+    if (!words) return fail(GOL_EINVAL, "null words");
+    std::vector<CopyDesc> d;
+    int rc = many_plan(hs, n, nwords, d, false);
+    if (rc) return rc;
+    const size_t dbytes = (n * sizeof(CopyDesc) + 255) & ~size_t(255);
+    Scratch st(dbytes + nwords * 8);
+    if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", nwords * 8);
+    CU(cudaMemcpyAsync(st.p, d.data(), n * sizeof(CopyDesc), cudaMemcpyHostToDevice, g_stream));
+    uint64_t *stage = (uint64_t *)((char *)st.p + dbytes);
+    CU(launch_gather_boards((const CopyDesc *)st.p, (int)n, stage, g_stream));
+    CU(cudaMemcpyAsync(words, stage, nwords * 8, cudaMemcpyDeviceToHost, g_stream));
+    return sync_stream();
 }
 
 int gol_get_region(gol_handle h, int64_t r0, int64_t c0, int64_t nr, int64_t nc, uint8_t *out) {

@@ -69,6 +69,15 @@ struct PersistArgs {
     int64_t timeout_ns; // bounded waits give up after this long without progress
 };
 
+// One board of a many-board transfer: `nwords` words of the board buffer
+// `board` live at word `offset` of a contiguous staging buffer.
+struct CopyDesc {
+    uint64_t *board;
+    int32_t *cur;       // scatter: reset to 0 (may be null)
+    int64_t offset;
+    int64_t nwords;
+};
+
 // Launchers (one translation unit per K).  Return cudaGetLastError().
 template <int K>
 cudaError_t launch_persistent(const PersistArgs &a, bool torus, int grid, cudaStream_t s);
@@ -91,6 +100,8 @@ cudaError_t launch_popcount_packed(const uint64_t *words, int64_t n, unsigned lo
                                    cudaStream_t s);
 cudaError_t launch_popcount_bytes(const uint8_t *cells, int64_t n, unsigned long long *out,
                                   cudaStream_t s);
+cudaError_t launch_scatter_boards(const CopyDesc *d, int n, const uint64_t *staging, cudaStream_t s);
+cudaError_t launch_gather_boards(const CopyDesc *d, int n, uint64_t *staging, cudaStream_t s);
 cudaError_t launch_int_probe(unsigned *sink, int iters, int grid, int block, cudaStream_t s);
 int int_probe_ops_per_iter();   // 32-bit integer operations per thread per probe iteration
 

@@ -173,6 +173,19 @@ __global__ void popcount_kernel(const T *__restrict__ v, int64_t n, unsigned lon
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
+// --- many boards <-> one contiguous staging buffer ----------------------------
+// block b copies the words of board b; a null `cur` is not written
+__global__ void scatter_boards_kernel(const CopyDesc *__restrict__ d, const uint64_t *__restrict__ staging) {
+    const CopyDesc c = d[blockIdx.x];
+    for (int64_t i = threadIdx.x; i < c.nwords; i += blockDim.x) c.board[i] = staging[c.offset + i];
+    if (threadIdx.x == 0 && c.cur) *c.cur = 0;
+}
+
+__global__ void gather_boards_kernel(const CopyDesc *__restrict__ d, uint64_t *__restrict__ staging) {
+    const CopyDesc c = d[blockIdx.x];
+    for (int64_t i = threadIdx.x; i < c.nwords; i += blockDim.x) staging[c.offset + i] = c.board[i];
+}
+
 // --- integer-pipe probe -------------------------------------------------------
 // Eight independent chains; per iteration and chain five LOP3 and one funnel
 // shift, the 20:4 LOP3:SHF ratio of one generation of a word.
@@ -255,6 +268,16 @@ cudaError_t launch_popcount_packed(const uint64_t *words, int64_t n, unsigned lo
 cudaError_t launch_popcount_bytes(const uint8_t *cells, int64_t n, unsigned long long *out,
                                   cudaStream_t s) {
     popcount_kernel<uint8_t><<<grid_for(n, kBlock, 8192), kBlock, 0, s>>>(cells, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_boards(const CopyDesc *d, int n, const uint64_t *staging, cudaStream_t s) {
+    if (n > 0) scatter_boards_kernel<<<n, kBlock, 0, s>>>(d, staging);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_boards(const CopyDesc *d, int n, uint64_t *staging, cudaStream_t s) {
+    if (n > 0) gather_boards_kernel<<<n, kBlock, 0, s>>>(d, staging);
     return cudaGetLastError();
 }
 

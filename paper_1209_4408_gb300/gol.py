@@ -41,7 +41,8 @@ GOL_OPT_WAIT_TIMEOUT_MS = 4
 # every symbol declared in include/gol.h
 EXPORTED = (
     "gol_create", "gol_create_ex", "gol_destroy", "gol_set", "gol_get", "gol_set_packed",
-    "gol_get_packed", "gol_set_packed_device", "gol_get_packed_device", "gol_get_region",
+    "gol_get_packed", "gol_set_packed_device", "gol_get_packed_device", "gol_set_packed_batch",
+    "gol_get_packed_batch", "gol_get_region",
     "gol_step", "gol_step_batch", "gol_population", "gol_generation", "gol_info", "gol_sync",
     "gol_set_stream", "gol_set_allocator", "gol_last_error", "gol_set_option", "gol_get_option",
     "gol_tune_set", "gol_tune_get", "gol_device_info", "gol_probe_int_throughput",
@@ -81,6 +82,8 @@ def load() -> ctypes.CDLL:
         "gol_get_packed": [vp, vp, sz],
         "gol_set_packed_device": [vp, vp, sz],
         "gol_get_packed_device": [vp, vp, sz],
+        "gol_set_packed_batch": [vp, sz, vp, sz],
+        "gol_get_packed_batch": [vp, sz, vp, sz],
         "gol_get_region": [vp, i64, i64, i64, i64, vp],
         "gol_step": [vp, i64],
         "gol_step_batch": [vp, vp, sz],
@@ -177,6 +180,25 @@ def gol_set_packed_device(h: int, dptr: int, nwords: int):
 
 def gol_get_packed_device(h: int, dptr: int, nwords: int):
     _check(load().gol_get_packed_device(h, dptr, nwords))
+
+
+def _handles(hs) -> np.ndarray:
+    return np.ascontiguousarray(np.array(list(hs), dtype=np.uint64))
+
+
+def gol_set_packed_batch(hs: Sequence[int], words: np.ndarray):
+    """``words``: the boards' packed states one after the other (1-D uint64)."""
+    h = _handles(hs)
+    a = np.ascontiguousarray(words, dtype=np.uint64).reshape(-1)
+    _check(load().gol_set_packed_batch(_ptr(h), h.size, _ptr(a), a.size))
+
+
+def gol_get_packed_batch(hs: Sequence[int], out: np.ndarray) -> np.ndarray:
+    h = _handles(hs)
+    if not (out.dtype == np.uint64 and out.flags.c_contiguous):
+        raise ValueError("out must be a contiguous uint64 array")
+    _check(load().gol_get_packed_batch(_ptr(h), h.size, _ptr(out), out.size))
+    return out
 
 
 def gol_get_region(h: int, r0: int, c0: int, nr: int, nc: int) -> np.ndarray:

@@ -301,3 +301,28 @@ def test_bounded_wait_times_out_and_context_survives(gol):
     assert gol.gol_debug_unfilled_wait(200) == gol.GOL_ETIMEOUT
     cells = synth.bernoulli_board(64, 128, 0.5, 1)
     assert_same(run_gpu(gol, cells, 9), oracle.run(cells, 9), "after timeout")
+
+
+def test_many_board_transfers(gol):
+    specs = synth.batch_specs(9, seed=21, side_hi=600, gen_lo=2, gen_hi=30)
+    boards = [gol.Board(s.rows, s.cols) for s in specs]
+    cells = [synth.bernoulli_board(s.rows, s.cols, s.density, s.seed) for s in specs]
+    flat = np.concatenate([synth.pack_cells(c).reshape(-1) for c in cells])
+    hs = [b.handle for b in boards]
+    gol.gol_set_packed_batch(hs, flat)
+    gol.step_batch(boards, [s.gens for s in specs])
+    out = np.empty_like(flat)
+    gol.gol_get_packed_batch(hs, out)
+    off = 0
+    for s, b, c in zip(specs, boards, cells):
+        n = s.rows * s.cols // 64
+        want = oracle.run(c, s.gens)
+        assert_same(oracle.unpack_words(out[off:off + n].reshape(s.rows, s.cols // 64)), want,
+                    "batch transfer board %d" % s.index)
+        assert_same(b.get(), want, "board %d" % s.index)
+        assert b.generation() == s.gens
+        off += n
+    with pytest.raises(gol.GolError):
+        gol.gol_set_packed_batch(hs, flat[:-1])
+    with pytest.raises(gol.GolError):
+        gol.gol_set_packed_batch(hs + hs[:1], np.concatenate([flat, flat[:specs[0].rows * specs[0].cols // 64]]))
