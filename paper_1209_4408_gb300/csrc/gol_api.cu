@@ -705,6 +705,7 @@ int gol_set_packed(gol_handle h, const uint64_t *words, size_t nwords) {
     h->cur = 0;
     h->generation = 0;
     CU(cudaMemcpyAsync(h->buf[0], words, nwords * 8, cudaMemcpyHostToDevice, g_stream));
+    CU(launch_convert((const uint64_t *)h->buf[0], (uint64_t *)h->buf[0], (int64_t)nwords, true, g_stream));
     return set_cur_device(h);
 }
 
@@ -714,7 +715,10 @@ int gol_get_packed(gol_handle h, uint64_t *words, size_t nwords) {
     if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board is not packed");
     if (nwords != (size_t)(h->rows * h->words))
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
-    CU(cudaMemcpyAsync(words, h->buf[h->cur], nwords * 8, cudaMemcpyDeviceToHost, g_stream));
+    Scratch st(nwords * 8);
+    if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", nwords * 8);
+    CU(launch_convert((const uint64_t *)h->buf[h->cur], (uint64_t *)st.p, (int64_t)nwords, false, g_stream));
+    CU(cudaMemcpyAsync(words, st.p, nwords * 8, cudaMemcpyDeviceToHost, g_stream));
     return sync_stream();
 }
 
@@ -726,7 +730,7 @@ int gol_set_packed_device(gol_handle h, const uint64_t *dwords, size_t nwords) {
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
     h->cur = 0;
     h->generation = 0;
-    CU(cudaMemcpyAsync(h->buf[0], dwords, nwords * 8, cudaMemcpyDeviceToDevice, g_stream));
+    CU(launch_convert(dwords, (uint64_t *)h->buf[0], (int64_t)nwords, true, g_stream));
     return set_cur_device(h);
 }
 
@@ -736,7 +740,7 @@ int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords) {
     if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board is not packed");
     if (nwords != (size_t)(h->rows * h->words))
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
-    CU(cudaMemcpyAsync(dwords, h->buf[h->cur], nwords * 8, cudaMemcpyDeviceToDevice, g_stream));
+    CU(launch_convert((const uint64_t *)h->buf[h->cur], dwords, (int64_t)nwords, false, g_stream));
     return GOL_OK;
 }
 

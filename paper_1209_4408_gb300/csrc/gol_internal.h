@@ -4,6 +4,15 @@
 // word k holds column 64k + j.  Each board owns two such buffers and a
 // device int `cur` naming the one that holds the current generation.
 //
+// Device-resident word layout.  The interchange layout (bit j of word k =
+// column 64k + j) is converted on every upload and download to the
+// resident layout, in which the low 32 bits of a word hold the word's even
+// columns (bit j = column 64k + 2j) and the high 32 bits its odd columns
+// (bit 32 + j = column 64k + 2j + 1).  With that split the east neighbour of
+// an even column and the west neighbour of an odd column sit at the same bit
+// of the other half, so a row's horizontal neighbour planes take 2 funnel
+// shifts per word instead of 4.
+//
 // A packed step is organised in "units": the rectangle of output cells one
 // warp produces per pass.  A pass advances a unit by kk <= K generations,
 // reading the previous pass's buffer (with a K-row and one-word halo) and
@@ -20,7 +29,7 @@ namespace gol {
 
 constexpr int kMaxNeighbours = 8;   // units whose output a unit's halo can touch
 constexpr int kTileWords = 30;      // output words of a tiled warp (32 lanes - 2 halo lanes)
-constexpr int kWarpsPerBlock = 4;   // persistent kernel: 128-thread blocks
+constexpr int kWarpsPerBlock = 2;   // persistent kernel: 64-thread blocks (fine occupancy steps)
 
 enum UnitMode : int32_t { kUnitFull = 0, kUnitTiled = 1 };
 
@@ -71,6 +80,33 @@ struct PersistArgs {
 
 // One board of a many-board transfer: `nwords` words of the board buffer
 // `board` live at word `offset` of a contiguous staging buffer.
+__host__ __device__ __forceinline__ uint64_t compress_even_bits(uint64_t v) {
+    v &= 0x5555555555555555ull;
+    v = (v | (v >> 1)) & 0x3333333333333333ull;
+    v = (v | (v >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+    v = (v | (v >> 4)) & 0x00FF00FF00FF00FFull;
+    v = (v | (v >> 8)) & 0x0000FFFF0000FFFFull;
+    return (v | (v >> 16)) & 0x00000000FFFFFFFFull;
+}
+__host__ __device__ __forceinline__ uint64_t spread_to_even_bits(uint64_t v) {
+    v &= 0x00000000FFFFFFFFull;
+    v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
+    v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
+    v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    v = (v | (v << 2)) & 0x3333333333333333ull;
+    return (v | (v << 1)) & 0x5555555555555555ull;
+}
+// interchange layout -> resident layout
+__host__ __device__ __forceinline__ uint64_t to_resident(uint64_t w) {
+    return compress_even_bits(w) | (compress_even_bits(w >> 1) << 32);
+}
+// resident layout -> interchange layout
+__host__ __device__ __forceinline__ uint64_t to_interchange(uint64_t w) {
+    return spread_to_even_bits(w) | (spread_to_even_bits(w >> 32) << 1);
+}
+// bit of column c (0 <= c < 64) of a resident word
+__host__ __device__ __forceinline__ int resident_bit(int c) { return (c & 1) ? 32 + (c >> 1) : (c >> 1); }
+
 struct CopyDesc {
     uint64_t *board;
     int32_t *cur;       // scatter: reset to 0 (may be null)
@@ -100,6 +136,7 @@ cudaError_t launch_popcount_packed(const uint64_t *words, int64_t n, unsigned lo
                                    cudaStream_t s);
 cudaError_t launch_popcount_bytes(const uint8_t *cells, int64_t n, unsigned long long *out,
                                   cudaStream_t s);
+cudaError_t launch_convert(const uint64_t *src, uint64_t *dst, int64_t n, bool to_res, cudaStream_t s);
 cudaError_t launch_scatter_boards(const CopyDesc *d, int n, const uint64_t *staging, cudaStream_t s);
 cudaError_t launch_gather_boards(const CopyDesc *d, int n, uint64_t *staging, cudaStream_t s);
 cudaError_t launch_int_probe(unsigned *sink, int iters, int grid, int block, cudaStream_t s);

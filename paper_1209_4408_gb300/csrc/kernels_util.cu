@@ -102,7 +102,7 @@ __global__ void pack_kernel(const uint8_t *__restrict__ cells, uint64_t *__restr
             }
         }
         if (any_high) atomicExch(bad, 1);
-        words[i] = w;
+        words[i] = to_resident(w);
     }
 }
 
@@ -116,7 +116,7 @@ __global__ void unpack_kernel(const uint64_t *__restrict__ words, uint8_t *__res
                               int64_t nwords) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t w = words[i];
+        const uint64_t w = to_interchange(words[i]);
         uint4 *p = reinterpret_cast<uint4 *>(cells + i * 64);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -143,7 +143,7 @@ __global__ void region_packed_kernel(const uint64_t *__restrict__ words, int64_t
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t y = i / nc, x = i - y * nc;
         const int64_t r = wrap(r0 + y, R), c = wrap(c0 + x, C);
-        out[i] = (uint8_t)((words[r * W + (c >> 6)] >> (c & 63)) & 1u);
+        out[i] = (uint8_t)((words[r * W + (c >> 6)] >> resident_bit((int)(c & 63))) & 1u);
     }
 }
 
@@ -173,17 +173,26 @@ __global__ void popcount_kernel(const T *__restrict__ v, int64_t n, unsigned lon
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
+// --- interchange <-> resident word layout ---------------------------------------
+__global__ void convert_kernel(const uint64_t *src, uint64_t *dst, int64_t n, bool to_res) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t w = src[i];
+        dst[i] = to_res ? to_resident(w) : to_interchange(w);
+    }
+}
+
 // --- many boards <-> one contiguous staging buffer ----------------------------
 // block b copies the words of board b; a null `cur` is not written
 __global__ void scatter_boards_kernel(const CopyDesc *__restrict__ d, const uint64_t *__restrict__ staging) {
     const CopyDesc c = d[blockIdx.x];
-    for (int64_t i = threadIdx.x; i < c.nwords; i += blockDim.x) c.board[i] = staging[c.offset + i];
+    for (int64_t i = threadIdx.x; i < c.nwords; i += blockDim.x) c.board[i] = to_resident(staging[c.offset + i]);
     if (threadIdx.x == 0 && c.cur) *c.cur = 0;
 }
 
 __global__ void gather_boards_kernel(const CopyDesc *__restrict__ d, uint64_t *__restrict__ staging) {
     const CopyDesc c = d[blockIdx.x];
-    for (int64_t i = threadIdx.x; i < c.nwords; i += blockDim.x) staging[c.offset + i] = c.board[i];
+    for (int64_t i = threadIdx.x; i < c.nwords; i += blockDim.x) staging[c.offset + i] = to_interchange(c.board[i]);
 }
 
 // --- integer-pipe probe -------------------------------------------------------
@@ -268,6 +277,11 @@ cudaError_t launch_popcount_packed(const uint64_t *words, int64_t n, unsigned lo
 cudaError_t launch_popcount_bytes(const uint8_t *cells, int64_t n, unsigned long long *out,
                                   cudaStream_t s) {
     popcount_kernel<uint8_t><<<grid_for(n, kBlock, 8192), kBlock, 0, s>>>(cells, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const uint64_t *src, uint64_t *dst, int64_t n, bool to_res, cudaStream_t s) {
+    if (n > 0) convert_kernel<<<grid_for(n, kBlock, 1 << 16), kBlock, 0, s>>>(src, dst, n, to_res);
     return cudaGetLastError();
 }
 

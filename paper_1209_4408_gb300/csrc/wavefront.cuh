@@ -2,18 +2,21 @@
 // run by a persistent dataflow scheduler.
 //
 // Arithmetic (Section 1 of the paper).  A lane holds one 64-cell word of a
-// row as two 32-bit halves.  For an input row it forms the row's
+// row in the resident layout (low half = even columns, high half = odd
+// columns, see gol_internal.h).  For an input row it forms the row's
 // horizontal three-cell sum per column as two bit planes:
-//     Wv = row shifted so bit j holds column j-1 (funnel shift, the carry bit
-//          comes from the west word, fetched from the neighbouring lane)
-//     Ev = row shifted so bit j holds column j+1
+//     Wv = the west neighbour of every column, Ev = the east neighbour; for
+//          the even half they are the odd half shifted by one (carry bit from
+//          the west word, fetched from the neighbouring lane) and the odd half
+//          itself, for the odd half the even half itself and the even half
+//          shifted by one (carry from the east word)
 //     s0 = Wv ^ x ^ Ev,  s1 = majority(Wv, x, Ev)          (s = s0 + 2 s1)
 // The nine-cell sum of a cell is S = s(row above) + s(row) + s(row below),
 // which includes the cell itself, so with n = S - alive the four
 // transitions reduce to  next = (S == 3) | (alive & (S == 4)).  That
 // predicate is evaluated bit-sliced with eight 3-input LOP3 operations per
-// 32-bit half (rule32).  One generation of a word costs 4 funnel shifts +
-// 20 LOP3 = 24 integer operations and 2 warp shuffles.
+// 32-bit half (rule32).  One generation of a word costs 2 funnel shifts +
+// 20 LOP3 = 22 integer operations and 2 warp shuffles.
 //
 // Temporal blocking.  A warp streams the rows of its unit top to bottom
 // through K pipeline stages held in registers; stage g turns generation g
@@ -204,12 +207,15 @@ __device__ __forceinline__ void run_unit_pass(const BoardDesc &bd, const UnitDes
             if (GUARD && j < 2 * g) break;                  // input of stage g not produced yet
             const uint32_t wh = __shfl_sync(kFull, xh, west_src) & west_mask;
             const uint32_t el = __shfl_sync(kFull, xl, east_src) & east_mask;
-            const uint32_t Wl = __funnelshift_l(wh, xl, 1);
-            const uint32_t Wh = __funnelshift_l(xl, xh, 1);
-            const uint32_t El = __funnelshift_r(xl, xh, 1);
-            const uint32_t Eh = __funnelshift_r(xh, el, 1);
-            const uint32_t n0l = lop3<kXor3>(Wl, xl, El), n0h = lop3<kXor3>(Wh, xh, Eh);
-            const uint32_t n1l = lop3<kMaj3>(Wl, xl, El), n1h = lop3<kMaj3>(Wh, xh, Eh);
+            // even columns (low half): west = odd column to the left = the
+            // high half shifted up by one, its bit 0 from the west word;
+            // east = the odd column to the right = the high half as is.
+            // odd columns (high half): west = the low half as is; east = the
+            // low half shifted down by one, its bit 31 from the east word.
+            const uint32_t Wl = __funnelshift_l(wh, xh, 1);
+            const uint32_t Eh = __funnelshift_r(xl, el, 1);
+            const uint32_t n0l = lop3<kXor3>(Wl, xl, xh), n0h = lop3<kXor3>(xl, xh, Eh);
+            const uint32_t n1l = lop3<kMaj3>(Wl, xl, xh), n1h = lop3<kMaj3>(xl, xh, Eh);
             uint32_t ol = 0, oh = 0;
             if (!GUARD || j >= 2 * g + 2) {
                 ol = rule32(p0l[g], p1l[g], c0l[g], c1l[g], n0l, n1l, cal[g]);
