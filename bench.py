@@ -49,7 +49,33 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-probe", action="store_true", help="skip the integer-throughput probe")
+    ap.add_argument("--serve-requests", type=int, default=600,
+                    help="requests of the served run added to the batch line (0 = skip)")
+    ap.add_argument("--serve-load", type=float, default=0.7,
+                    help="offered load of the served run as a fraction of the measured batched GCUPS")
+    ap.add_argument("--fcfs-requests", type=int, default=24,
+                    help="requests of the same trace served one at a time (baseline)")
     return ap.parse_args()
+
+
+def rank_batch(specs, rank: int):
+    """Weak scaling: every rank steps its own copy of the batch; rank r > 0
+    draws its boards from seeds derived from the rank."""
+    if rank == 0:
+        return list(specs)
+    return [synth.BoardSpec(s.index, s.rows, s.cols, s.density, s.gens, synth.derive_seed(s.seed, rank))
+            for s in specs]
+
+
+def max_over_ranks(ms: float, dist, device=None) -> float:
+    """The slowest rank's time (the job finishes when the last rank does)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_env():
@@ -142,6 +168,34 @@ def cpu_oracle_sample(specs, seconds: float, threads: int = 1):
 
 
 # ---------------------------------------------------------------------------
+# served request stream (continuous batching)
+# ---------------------------------------------------------------------------
+def served_run(gol, n_req, load, capacity_gcups, budget_bytes, fcfs_n, seed=synth.SEED_SERVE):
+    """Poisson request stream at `load` x the measured batched capacity,
+    served by the continuous-batching loop; then a prefix of the same trace
+    served one request at a time."""
+    from paper_1209_4408_gb300 import serve
+
+    probe = synth.request_stream(n_req, 1.0, seed=seed)
+    mean_work = sum(r.work for r in probe) / max(1, len(probe))
+    rate = load * capacity_gcups * 1e9 / mean_work
+    reqs = synth.request_stream(n_req, rate, seed=seed)
+    jobs = [serve.Job(r.index, r.arrival_s, r.rows, r.cols, r.gens,
+                      synth.bernoulli_words(r.rows, r.cols, r.density, r.seed)) for r in reqs]
+    st = serve.Server(budget_bytes=budget_bytes).run(jobs)
+    out = st.summary()
+    out.update({"rate_per_s": round(rate, 3), "offered_load": load, "budget_bytes": budget_bytes,
+                "workload": "Poisson arrivals; sides log-uniform [32, 8192] rounded to x64; density U(0.1,0.6);"
+                            " gens log-uniform [10, 1e5]; first %d requests of the seeded stream" % n_req})
+    if fcfs_n > 0:
+        fj = [serve.Job(j.rid, j.arrival_s, j.rows, j.cols, j.gens, j.words) for j in jobs[:fcfs_n]]
+        fs = serve.serve_fcfs(fj).summary()
+        out["fcfs"] = {k: fs[k] for k in ("requests", "p50_ms", "p99_ms", "mean_ms", "gcups", "makespan_s")}
+        out["fcfs"]["sample"] = "first %d requests of the same trace, one at a time with gol_step" % fcfs_n
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args, rank, world, local):
@@ -167,11 +221,7 @@ def run_gpu(args, rank, world, local):
 
     # ---- workload -----------------------------------------------------------
     if args.workload == "batch":
-        specs = synth.batch_specs(args.boards)
-        # weak scaling: each rank steps its own copy of the batch with its own seeds
-        if rank:
-            specs = [synth.BoardSpec(s.index, s.rows, s.cols, s.density, s.gens,
-                                     synth.derive_seed(s.seed, rank)) for s in specs]
+        specs = rank_batch(synth.batch_specs(args.boards), rank)
         workload = "batch of %d uneven toroidal packed boards (rows, cols log-uniform [32, 2048] " \
                    "rounded to x64; density U(0.1,0.6); gens log-uniform [100, 5000])" % len(specs)
     elif args.workload == "single":
@@ -233,11 +283,7 @@ def run_gpu(args, rank, world, local):
     clocks = clk.summary()
     ms_total = t_start.elapsed_time(t_end)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = ms_total / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms_total / args.steps, dist, "cuda")
     value = total_cells_gens * world / (ms * 1e-3) / 1e9
 
     # ---- plain loop: the same boards stepped one at a time -----------------------
@@ -324,6 +370,9 @@ def run_gpu(args, rank, world, local):
         out["roofline"] = roofline
     for b in boards:
         b.close()
+    if args.workload == "batch" and args.serve_requests > 0:
+        out["served"] = served_run(gol, args.serve_requests, args.serve_load, value / world, 120 << 30,
+                                   args.fcfs_requests)
     gol.gol_set_allocator(None, None)
     if rank == 0:
         if not args.no_cpu:

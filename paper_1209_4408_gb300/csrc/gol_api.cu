@@ -8,7 +8,6 @@
 #include <map>
 #include <memory>
 #include <mutex>
-#include <set>
 #include <string>
 #include <unordered_set>
 #include <vector>
@@ -247,20 +246,32 @@ cudaError_t launch_for(int K, const PersistArgs &a, bool torus, int grid, cudaSt
     return cudaErrorInvalidValue;
 }
 
-// split rows [0, R) into nb balanced blocks; block i = [R*i/nb, R*(i+1)/nb)
-void build_units(const gol_board *h, int bindex, int K, int tile_rows, std::vector<UnitDesc> &units,
-                 int32_t *nunits_out) {
-    const int R = (int)h->rows, W = (int)h->words;
-    const bool full = W <= 32;
-    const int S = full ? std::max(1, 32 / W) : 1;
-    const int nt = full ? 1 : (W + kTileWords - 1) / kTileWords;
-    // rows per unit: S segments of tile_rows rows (FULL) or tile_rows (TILED)
-    int64_t target = (int64_t)S * std::max(1, tile_rows);
-    int nb = (int)std::max<int64_t>(1, (R + target - 1) / target);
+// Units of one board: nb balanced row blocks (block i = [R*i/nb, R*(i+1)/nb))
+// times nt word tiles.
+struct UnitGrid {
+    int nb, nt, S;
+    bool full;
+};
+
+UnitGrid unit_grid(int64_t rows, int64_t words, int K, int tile_rows) {
+    UnitGrid g;
+    const int R = (int)rows, W = (int)words;
+    g.full = W <= 32;
+    g.S = g.full ? std::max(1, 32 / W) : 1;
+    g.nt = g.full ? 1 : (W + kTileWords - 1) / kTileWords;
+    // rows per unit: S segments of tile_rows rows (full rows) or tile_rows (tiles)
+    const int64_t target = (int64_t)g.S * std::max(1, tile_rows);
+    g.nb = (int)std::max<int64_t>(1, (R + target - 1) / target);
     // with more than one block every block must be >= K rows so that a halo
     // reaches only the adjacent blocks
-    if (nb > 1 && R / nb < K) nb = std::max(1, R / K);
-    const int first = (int)units.size();
+    if (g.nb > 1 && R / g.nb < K) g.nb = std::max(1, R / K);
+    return g;
+}
+
+// Writes the g.nb * g.nt units of a board to out[0..); unit ids are
+// first + index.  Uses no dynamic memory.
+void fill_units(int64_t rows, int64_t words, int bindex, const UnitGrid &g, UnitDesc *out, int first) {
+    const int R = (int)rows, W = (int)words, nb = g.nb, nt = g.nt, S = g.S;
     for (int i = 0; i < nb; ++i) {
         const int r0 = (int)((int64_t)R * i / nb), r1 = (int)((int64_t)R * (i + 1) / nb);
         const int bh = r1 - r0;
@@ -269,7 +280,7 @@ void build_units(const gol_board *h, int bindex, int K, int tile_rows, std::vect
             u.board = bindex;
             u.r0 = r0;
             u.r_end = r1;
-            if (full) {
+            if (g.full) {
                 u.mode = kUnitFull;
                 u.H = (bh + S - 1) / S;
                 u.S = (bh + u.H - 1) / u.H;
@@ -282,25 +293,38 @@ void build_units(const gol_board *h, int bindex, int K, int tile_rows, std::vect
                 u.w0 = (int)((int64_t)W * t / nt);
                 u.U = (int)((int64_t)W * (t + 1) / nt) - u.w0;
             }
+            // neighbours: adjacent row blocks x adjacent tiles (wrapping), minus self
             u.nnb = 0;
-            units.push_back(u);
-        }
-    }
-    // neighbours: adjacent row blocks x adjacent tiles (wrapping), minus self
-    for (int i = 0; i < nb; ++i)
-        for (int t = 0; t < nt; ++t) {
-            UnitDesc &u = units[first + i * nt + t];
-            std::set<int> nbs;
-            const int di[3] = {-1, 0, 1};
-            for (int a : di)
-                for (int b : di) {
+            for (int a = -1; a <= 1; ++a)
+                for (int b = -1; b <= 1; ++b) {
                     const int ii = ((i + a) % nb + nb) % nb, tt = ((t + b) % nt + nt) % nt;
                     const int id = first + ii * nt + tt;
-                    if (id != first + i * nt + t) nbs.insert(id);
+                    if (id == first + i * nt + t) continue;
+                    bool seen = false;
+                    for (int k = 0; k < u.nnb; ++k) seen = seen || u.nb[k] == id;
+                    if (!seen) u.nb[u.nnb++] = id;
                 }
-            for (int id : nbs) u.nb[u.nnb++] = id;
+            out[i * nt + t] = u;
         }
-    *nunits_out = nb * nt;
+    }
+}
+
+void build_units(const gol_board *h, int bindex, int K, int tile_rows, std::vector<UnitDesc> &units,
+                 int32_t *nunits_out) {
+    const UnitGrid g = unit_grid(h->rows, h->words, K, tile_rows);
+    const size_t first = units.size();
+    units.resize(first + (size_t)g.nb * g.nt);
+    fill_units(h->rows, h->words, bindex, g, units.data() + first, (int)first);
+    *nunits_out = g.nb * g.nt;
+}
+
+// Tile rows of a board with `npass` passes under a chain cap (see build_plan).
+int capped_tile_rows(int rows, int64_t npass, int K, double chain_cap) {
+    if ((double)npass * (rows + 2 * K) > chain_cap) {
+        const int h = (int)(chain_cap / (double)npass) - 2 * K;
+        rows = std::max(std::max(8, K), std::min(rows, h));
+    }
+    return rows;
 }
 
 int build_plan(Plan &P) {
@@ -340,13 +364,8 @@ int build_plan(Plan &P) {
         work += units * np * (double)(hrows[i] + 2 * P.K);
     }
     const double chain_cap = g_opt_rows ? 1e300 : 0.5 * work / (double)slots;
-    for (size_t i = 0; i < n; ++i) {
-        const int64_t np = (P.gens[i] + P.K - 1) / P.K;
-        if ((double)np * (hrows[i] + 2 * P.K) > chain_cap) {
-            const int h = (int)(chain_cap / (double)np) - 2 * P.K;
-            hrows[i] = std::max(std::max(8, P.K), std::min(hrows[i], h));
-        }
-    }
+    for (size_t i = 0; i < n; ++i)
+        hrows[i] = capped_tile_rows(hrows[i], (P.gens[i] + P.K - 1) / P.K, P.K, chain_cap);
     P.total_tasks = 0;
     for (size_t i = 0; i < n; ++i) {
         gol_board *h = P.hs[i];
@@ -1033,3 +1052,4 @@ int gol_debug_unfilled_wait(int64_t timeout_ms) {
 }
 
 }  // extern "C"
+
