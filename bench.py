@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-INT_OPS_PER_WORD_GEN = 24          # 4 funnel shifts + 20 LOP3 per 64-cell word per generation
+INT_OPS_PER_WORD_GEN = 22          # 2 funnel shifts + 20 LOP3 per 64-cell word per generation
 
 
 def parse():
