@@ -101,6 +101,30 @@ int gol_get_packed_batch(const gol_handle *hs, size_t n, uint64_t *words, size_t
  * size, so windows may straddle the wrap.  nr, nc >= 0. */
 int gol_get_region(gol_handle h, int64_t r0, int64_t c0, int64_t nr, int64_t nc, uint8_t *out);
 
+/* Allocation-free stepping of one packed torus or bounded board held by the
+ * caller (the paper has no counterpart: this entry exists for callers that
+ * cannot allocate device memory while they run, e.g. code inside its own
+ * memory pool or with a fixed reserved budget).
+ *   d_board  device memory, rows x cols/64 words in the packed layout; holds
+ *            the initial state on entry and the state after `generations`
+ *            steps on return;
+ *   d_spare  device memory of the same size, distinct from d_board; its
+ *            contents are overwritten;
+ *   stream   the cudaStream_t to run on (null = default stream).
+ * rows >= 1, cols a multiple of 64 and at most 30*4096*64 = 7864320,
+ * generations >= 0.  The call allocates nothing: the scheduler's workspace
+ * is a file-scope device array of about 1.3 MiB that every GPU loading the
+ * library holds until the process exits.  The first call on a device looks
+ * up that array's device address; make it before any stream capture.  All
+ * calls share the array and it keeps the last call's contents (every call
+ * re-initialises what must start at zero), so calls that overlapped on the
+ * GPU would race: the library serialises its calls and each call waits for
+ * its stream before returning.  Returns GOL_EINVAL for bad arguments or a
+ * board too wide for the workspace, GOL_ETIMEOUT if a bounded device wait
+ * gave up, GOL_ECUDA for CUDA errors. */
+int gol_step_packed_noalloc(uint64_t *d_board, uint64_t *d_spare, int64_t rows, int64_t cols, int torus,
+                            int64_t generations, void *stream);
+
 /* Advances the board by `generations` >= 0 steps (0 is a no-op).
  * Asynchronous; the result is bit-identical to applying the step of
  * Section 1 `generations` times.  Packed boards run several generations

@@ -1053,3 +1053,126 @@ int gol_debug_unfilled_wait(int64_t timeout_ms) {
 
 }  // extern "C"
 
+// ===========================================================================
+// Stepping a packed board without allocating device memory
+// ===========================================================================
+// Some callers cannot allocate device memory while they step a board: code
+// running inside a memory pool or allocator of its own, code that must not
+// synchronise with the device the way cudaMalloc/cudaFree may, or code that
+// has a fixed memory budget reserved in advance.  This entry point takes the
+// board and a spare buffer from the caller and keeps the scheduler's
+// workspace (unit table, pass counters, work queue, status words) in one
+// file-scope device array instead of allocating it.
+namespace {
+constexpr int kStaticMaxUnits = 4096;          // units of one board
+constexpr int kStaticMaxTasks = 1 << 18;       // queue slots per launch
+constexpr size_t kSaUnits = 256;               // offsets in the static workspace
+constexpr size_t kSaDone = kSaUnits + sizeof(UnitDesc) * kStaticMaxUnits;
+constexpr size_t kSaClaimed = kSaDone + 4 * (size_t)kStaticMaxUnits;
+constexpr size_t kSaCtr = kSaClaimed + 4 * (size_t)kStaticMaxUnits;
+constexpr size_t kSaStatus = kSaCtr + 256;     // [0] status, [1] current buffer
+constexpr size_t kSaRing = kSaStatus + 256;
+constexpr size_t kStaticBytes = kSaRing + 4 * (size_t)kStaticMaxTasks;   // about 1.3 MiB
+
+// Shared by every call on a device and kept until the process exits.
+static __device__ __align__(256) unsigned char g_static_workspace[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+char *g_static_base[kMaxDevices] = {};          // device address of the array, per device
+UnitDesc g_static_units[kStaticMaxUnits];       // host copy of the unit table
+}  // namespace
+
+extern "C" int gol_step_packed_noalloc(uint64_t *d_board, uint64_t *d_spare, int64_t rows, int64_t cols,
+                                       int torus, int64_t generations, void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!d_board || !d_spare || d_board == d_spare) return fail(GOL_EINVAL, "need two distinct device buffers");
+    if (rows < 1 || cols < 64 || cols % 64 != 0) return fail(GOL_EINVAL, "need rows >= 1 and cols a multiple of 64");
+    if (rows > (int64_t(1) << 30)) return fail(GOL_EINVAL, "rows = %lld exceeds 2^30", (long long)rows);
+    if (generations < 0) return fail(GOL_EINVAL, "negative generation count");
+    const int64_t W = cols / 64;
+    if ((W + kTileWords - 1) / kTileWords > kStaticMaxUnits)
+        return fail(GOL_EINVAL, "cols = %lld exceeds the static workspace (at most %lld columns)", (long long)cols,
+                    (long long)kTileWords * kStaticMaxUnits * 64);
+    if (generations == 0) return GOL_OK;
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(GOL_EINVAL, "device %d out of range", dev);
+    if (!g_static_base[dev]) {   // first call on this device
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_workspace);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static workspace");
+        g_static_base[dev] = (char *)p;
+    }
+    char *base = g_static_base[dev];
+    cudaStream_t s = (cudaStream_t)stream;
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+
+    // plan: generations per pass and unit height as for gol_step, then taller
+    // units until the board needs at most kStaticMaxUnits of them
+    const TuneEntry te = tune_lookup(rows, cols);
+    const int K = supported_k(std::max(1, te.k));
+    int bps = 1;
+    CU(occupancy_for(K, torus != 0, &bps));
+    const int64_t slots = (int64_t)sms * std::max(1, bps) * kWarpsPerBlock;
+    const int64_t npass_all = (generations + K - 1) / K;
+    int h = std::max(1, te.rows);
+    {
+        const UnitGrid g0 = unit_grid(rows, W, K, h);
+        const double work = (double)g0.nb * g0.nt * npass_all * (h + 2 * K);
+        if (!g_opt_rows) h = capped_tile_rows(h, npass_all, K, 0.5 * work / (double)slots);
+    }
+    UnitGrid g = unit_grid(rows, W, K, h);
+    while (g.nb * g.nt > kStaticMaxUnits) {
+        h = std::max(h + 1, (int)((int64_t)h * g.nb * g.nt / kStaticMaxUnits + 1));
+        g = unit_grid(rows, W, K, h);
+    }
+    const int nunits = g.nb * g.nt;
+    fill_units(rows, W, 0, g, g_static_units, 0);
+
+    CU(cudaMemcpyAsync(base + kSaUnits, g_static_units, sizeof(UnitDesc) * nunits, cudaMemcpyHostToDevice, s));
+    CU(cudaMemsetAsync(base + kSaStatus, 0, 8, s));   // status and current-buffer words
+    const int64_t nwords = rows * W;
+    CU(launch_convert(d_board, d_board, nwords, true, s));
+
+    PersistArgs a{};
+    a.boards = (const BoardDesc *)base;
+    a.units = (const UnitDesc *)(base + kSaUnits);
+    a.done = (int32_t *)(base + kSaDone);
+    a.claimed = (int32_t *)(base + kSaClaimed);
+    a.ctr = (int32_t *)(base + kSaCtr);
+    a.ring = (int32_t *)(base + kSaRing);
+    a.sticky = (int32_t *)(base + kSaStatus);
+    a.nunits = nunits;
+    a.timeout_ns = g_opt_timeout_ms * 1000000ll;
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)sms * std::max(1, bps), (nunits + kWarpsPerBlock - 1) / kWarpsPerBlock));
+    // launches of at most kStaticMaxTasks tasks each
+    const int64_t passes_per_launch = std::max<int64_t>(1, kStaticMaxTasks / nunits);
+    int cur = 0;
+    for (int64_t left = generations; left > 0;) {
+        const int64_t gens = std::min<int64_t>(left, passes_per_launch * K);
+        BoardDesc bd{};
+        bd.buf[0] = d_board;
+        bd.buf[1] = d_spare;
+        bd.cur = (int32_t *)(base + kSaStatus) + 1;
+        bd.R = (int32_t)rows;
+        bd.W = (int32_t)W;
+        bd.gens = (int32_t)gens;
+        bd.npass = (int32_t)((gens + K - 1) / K);
+        bd.nunits = nunits;
+        CU(cudaMemcpyAsync(base, &bd, sizeof bd, cudaMemcpyHostToDevice, s));
+        a.total_tasks = nunits * bd.npass;
+        CU(launch_sched_init(a, 1, s));
+        CU(launch_for(K, a, torus != 0, grid, s));
+        cur ^= bd.npass & 1;
+        left -= gens;
+    }
+    // back to the interchange layout, into d_board
+    CU(launch_convert(cur ? d_spare : d_board, d_board, nwords, false, s));
+    CU(cudaStreamSynchronize(s));
+    int32_t status = 0;
+    CU(cudaMemcpy(&status, base + kSaStatus, sizeof status, cudaMemcpyDeviceToHost));
+    if (status) return fail(status, "a device-side bounded wait gave up (status %d); the board is not valid", status);
+    return GOL_OK;
+}

@@ -46,7 +46,7 @@ EXPORTED = (
     "gol_step", "gol_step_batch", "gol_population", "gol_generation", "gol_info", "gol_sync",
     "gol_set_stream", "gol_set_allocator", "gol_last_error", "gol_set_option", "gol_get_option",
     "gol_tune_set", "gol_tune_get", "gol_device_info", "gol_probe_int_throughput",
-    "gol_debug_unfilled_wait",
+    "gol_debug_unfilled_wait", "gol_step_packed_noalloc",
 )
 
 
@@ -101,6 +101,7 @@ def load() -> ctypes.CDLL:
         "gol_device_info": [P(i32), P(i64), P(i32)],
         "gol_probe_int_throughput": [P(ctypes.c_double), P(ctypes.c_double)],
         "gol_debug_unfilled_wait": [i64],
+        "gol_step_packed_noalloc": [vp, vp, i64, i64, i32, i64, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -217,6 +218,14 @@ def gol_step_batch(hs: Sequence[int], generations: Iterable[int]):
     if hs_a.size != g_a.size:
         raise ValueError("handles and generation counts differ in length")
     _check(load().gol_step_batch(_ptr(hs_a), _ptr(g_a), hs_a.size))
+
+
+def gol_step_packed_noalloc(d_board: int, d_spare: int, rows: int, cols: int, torus: bool,
+                            generations: int, stream=None):
+    """Steps the packed board at device address ``d_board`` in place, using
+    ``d_spare`` (same size) as its second buffer; allocates no device memory."""
+    sp = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(load().gol_step_packed_noalloc(d_board, d_spare, rows, cols, int(bool(torus)), int(generations), sp))
 
 
 def gol_population(h: int) -> int:
