@@ -178,11 +178,17 @@ const char *gol_last_error(void);
  *   GOL_OPT_USE_GRAPHS     1 = capture/replay gol_step_batch in CUDA graphs
  *   GOL_OPT_WAIT_TIMEOUT_MS  limit of the device-side bounded waits
  *                          (default 5000 ms without progress)
+ *   GOL_OPT_ORIENTATION    storage of packed boards created afterwards with
+ *                          rows % 64 == 0: 0 = the library stores the board
+ *                          transposed when that fills the warps better,
+ *                          1 = never transposed, 2 = always transposed.  The
+ *                          interchange layout and every result are the same.
  * Unknown keys or values are GOL_EINVAL. */
 #define GOL_OPT_GENS_PER_PASS 1
 #define GOL_OPT_TILE_ROWS 2
 #define GOL_OPT_USE_GRAPHS 3
 #define GOL_OPT_WAIT_TIMEOUT_MS 4
+#define GOL_OPT_ORIENTATION 5
 int gol_set_option(int key, int64_t value);
 int gol_get_option(int key, int64_t *value);
 

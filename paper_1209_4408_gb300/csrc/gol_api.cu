@@ -29,6 +29,13 @@ struct gol_board {
     void (*free_fn)(void *, void *) = nullptr;
     void *alloc_ctx = nullptr;
     uint64_t serial = 0;                     // identity for the plan cache
+    // Packed boards may be stored transposed (stored row c holds column c of
+    // the board): the step is symmetric under transposition, and a board
+    // whose columns fit the warp lanes better that way runs faster.  The
+    // stored geometry is srows x swords; the interchange layout is always the
+    // board's own rows x words.
+    int transposed = 0;
+    int64_t srows = 0, swords = 0;
 };
 
 namespace {
@@ -66,7 +73,7 @@ cudaStream_t g_stream = nullptr;
 void *(*g_alloc)(size_t, void *) = nullptr;
 void (*g_free)(void *, void *) = nullptr;
 void *g_alloc_ctx = nullptr;
-int64_t g_opt_k = 0, g_opt_rows = 0, g_opt_graphs = 1, g_opt_timeout_ms = 5000;
+int64_t g_opt_k = 0, g_opt_rows = 0, g_opt_graphs = 1, g_opt_timeout_ms = 5000, g_opt_orient = 0;
 uint64_t g_serial = 0;
 
 struct DeviceState {
@@ -174,7 +181,7 @@ std::pair<int, int> size_class(int64_t rows, int64_t cols) {
 }
 TuneEntry tune_lookup(int64_t rows, int64_t cols) {
     auto it = g_tune.find(size_class(rows, cols));
-    TuneEntry t{6, 32};
+    TuneEntry t{6, 96};
     if (it != g_tune.end()) t = it->second;
     if (g_opt_k) t.k = (int)g_opt_k;
     if (g_opt_rows) t.rows = (int)g_opt_rows;
@@ -311,11 +318,26 @@ void fill_units(int64_t rows, int64_t words, int bindex, const UnitGrid &g, Unit
 
 void build_units(const gol_board *h, int bindex, int K, int tile_rows, std::vector<UnitDesc> &units,
                  int32_t *nunits_out) {
-    const UnitGrid g = unit_grid(h->rows, h->words, K, tile_rows);
+    const UnitGrid g = unit_grid(h->srows, h->swords, K, tile_rows);
     const size_t first = units.size();
     units.resize(first + (size_t)g.nb * g.nt);
-    fill_units(h->rows, h->words, bindex, g, units.data() + first, (int)first);
+    fill_units(h->srows, h->swords, bindex, g, units.data() + first, (int)first);
     *nunits_out = g.nb * g.nt;
+}
+
+// Fraction of the lane work of a pass that produces cells: lanes holding
+// words of the board (segments of full rows, or 30-word tiles) times the
+// share of stage rows that are not halo recomputation.
+double lane_efficiency(int64_t rows, int64_t words, int K, int tile_rows) {
+    const UnitGrid g = unit_grid(rows, words, K, tile_rows);
+    double useful = 0, work = 0;
+    for (int i = 0; i < g.nb; ++i) {
+        const int64_t bh = rows * (i + 1) / g.nb - rows * i / g.nb;
+        const int64_t h = g.full ? (bh + g.S - 1) / g.S : bh;
+        useful += (double)bh * words * K;
+        work += 32.0 * g.nt * ((double)h * K + (double)K * (K - 1));
+    }
+    return work > 0 ? useful / work : 0;
 }
 
 // Tile rows of a board with `npass` passes under a chain cap (see build_plan).
@@ -339,7 +361,7 @@ int build_plan(Plan &P) {
         const int64_t work = P.hs[i]->rows * P.hs[i]->cols * P.gens[i];
         if (work > best_work) {
             best_work = work;
-            K = tune_lookup(P.hs[i]->rows, P.hs[i]->cols).k;
+            K = tune_lookup(P.hs[i]->srows, P.hs[i]->swords * 64).k;
         }
     }
     P.K = supported_k(std::max(1, K));
@@ -356,11 +378,11 @@ int build_plan(Plan &P) {
     for (size_t i = 0; i < n; ++i) {
         const gol_board *h = P.hs[i];
         const int64_t np = (P.gens[i] + P.K - 1) / P.K;
-        hrows[i] = std::max(1, tune_lookup(h->rows, h->cols).rows);
-        const int W = (int)h->words;
+        hrows[i] = std::max(1, tune_lookup(h->srows, h->swords * 64).rows);
+        const int W = (int)h->swords;
         const int S = W <= 32 ? std::max(1, 32 / W) : 1;
         const int nt = W <= 32 ? 1 : (W + kTileWords - 1) / kTileWords;
-        const double units = std::ceil((double)h->rows / ((double)S * hrows[i])) * nt;
+        const double units = std::ceil((double)h->srows / ((double)S * hrows[i])) * nt;
         work += units * np * (double)(hrows[i] + 2 * P.K);
     }
     const double chain_cap = g_opt_rows ? 1e300 : 0.5 * work / (double)slots;
@@ -373,8 +395,8 @@ int build_plan(Plan &P) {
         bd.buf[0] = (uint64_t *)h->buf[0];
         bd.buf[1] = (uint64_t *)h->buf[1];
         bd.cur = h->dev_cur;
-        bd.R = (int32_t)h->rows;
-        bd.W = (int32_t)h->words;
+        bd.R = (int32_t)h->srows;
+        bd.W = (int32_t)h->swords;
         bd.gens = (int32_t)P.gens[i];
         bd.npass = (int32_t)((P.gens[i] + P.K - 1) / P.K);
         build_units(h, (int)i, P.K, hrows[i], P.units, &bd.nunits);
@@ -620,6 +642,22 @@ int gol_create_ex(int64_t rows, int64_t cols, int torus, int layout, gol_handle 
     h->free_fn = g_free;
     h->alloc_ctx = g_alloc_ctx;
     h->serial = ++g_serial;
+    h->srows = rows;
+    h->swords = h->words;
+    if (layout == GOL_LAYOUT_PACKED && rows % 64 == 0 && g_opt_orient != 1) {
+        bool t = g_opt_orient == 2;
+        if (!t) {
+            const TuneEntry a = tune_lookup(rows, cols), b = tune_lookup(cols, rows);
+            const double ea = lane_efficiency(rows, cols / 64, supported_k(a.k), a.rows);
+            const double eb = lane_efficiency(cols, rows / 64, supported_k(b.k), b.rows);
+            t = eb > 1.02 * ea;
+        }
+        if (t) {
+            h->transposed = 1;
+            h->srows = cols;
+            h->swords = rows / 64;
+        }
+    }
     h->buf[0] = dev_alloc(h->buf_bytes, h->alloc_fn, h->alloc_ctx);
     h->buf[1] = dev_alloc(h->buf_bytes, h->alloc_fn, h->alloc_ctx);
     h->dev_cur = (int32_t *)dev_alloc(256, h->alloc_fn, h->alloc_ctx);
@@ -688,7 +726,9 @@ int gol_set(gol_handle h, const uint8_t *cells, size_t n) {
         int32_t *bad = (int32_t *)((char *)st.p + flag_off);
         CU(cudaMemsetAsync(bad, 0, sizeof(int32_t), g_stream));
         CU(cudaMemcpyAsync(st.p, cells, n, cudaMemcpyHostToDevice, g_stream));
-        CU(launch_pack((const uint8_t *)st.p, (uint64_t *)h->buf[0], h->rows, h->words, bad, g_stream));
+        CU(launch_pack((const uint8_t *)st.p, (uint64_t *)h->buf[1], h->rows, h->words, bad, g_stream));
+        CU(launch_orient((const uint64_t *)h->buf[1], (uint64_t *)h->buf[0], h->rows, h->words, h->transposed, true,
+                         g_stream));
         int32_t bad_h = 0;
         CU(cudaMemcpyAsync(&bad_h, bad, sizeof bad_h, cudaMemcpyDeviceToHost, g_stream));
         CU(cudaStreamSynchronize(g_stream));
@@ -708,9 +748,12 @@ int gol_get(gol_handle h, uint8_t *cells, size_t n) {
         CU(cudaMemcpyAsync(cells, h->buf[h->cur], n, cudaMemcpyDeviceToHost, g_stream));
         return sync_stream();
     }
-    Scratch st(n);
+    const size_t woff = (n + 255) & ~size_t(255);
+    Scratch st(woff + n / 8);
     if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", n);
-    CU(launch_unpack((const uint64_t *)h->buf[h->cur], (uint8_t *)st.p, h->rows, h->words, g_stream));
+    uint64_t *words = (uint64_t *)((char *)st.p + woff);
+    CU(launch_orient((const uint64_t *)h->buf[h->cur], words, h->rows, h->words, h->transposed, false, g_stream));
+    CU(launch_unpack(words, (uint8_t *)st.p, h->rows, h->words, g_stream));
     CU(cudaMemcpyAsync(cells, st.p, n, cudaMemcpyDeviceToHost, g_stream));
     return sync_stream();
 }
@@ -723,8 +766,9 @@ int gol_set_packed(gol_handle h, const uint64_t *words, size_t nwords) {
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
     h->cur = 0;
     h->generation = 0;
-    CU(cudaMemcpyAsync(h->buf[0], words, nwords * 8, cudaMemcpyHostToDevice, g_stream));
-    CU(launch_convert((const uint64_t *)h->buf[0], (uint64_t *)h->buf[0], (int64_t)nwords, true, g_stream));
+    CU(cudaMemcpyAsync(h->buf[1], words, nwords * 8, cudaMemcpyHostToDevice, g_stream));
+    CU(launch_orient((const uint64_t *)h->buf[1], (uint64_t *)h->buf[0], h->rows, h->words, h->transposed, true,
+                     g_stream));
     return set_cur_device(h);
 }
 
@@ -736,7 +780,8 @@ int gol_get_packed(gol_handle h, uint64_t *words, size_t nwords) {
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
     Scratch st(nwords * 8);
     if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", nwords * 8);
-    CU(launch_convert((const uint64_t *)h->buf[h->cur], (uint64_t *)st.p, (int64_t)nwords, false, g_stream));
+    CU(launch_orient((const uint64_t *)h->buf[h->cur], (uint64_t *)st.p, h->rows, h->words, h->transposed, false,
+                     g_stream));
     CU(cudaMemcpyAsync(words, st.p, nwords * 8, cudaMemcpyDeviceToHost, g_stream));
     return sync_stream();
 }
@@ -749,7 +794,8 @@ int gol_set_packed_device(gol_handle h, const uint64_t *dwords, size_t nwords) {
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
     h->cur = 0;
     h->generation = 0;
-    CU(launch_convert(dwords, (uint64_t *)h->buf[0], (int64_t)nwords, true, g_stream));
+    if (dwords == h->buf[0] || dwords == h->buf[1]) return fail(GOL_EINVAL, "source is the board's own buffer");
+    CU(launch_orient(dwords, (uint64_t *)h->buf[0], h->rows, h->words, h->transposed, true, g_stream));
     return set_cur_device(h);
 }
 
@@ -759,7 +805,7 @@ int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords) {
     if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board is not packed");
     if (nwords != (size_t)(h->rows * h->words))
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
-    CU(launch_convert((const uint64_t *)h->buf[h->cur], dwords, (int64_t)nwords, false, g_stream));
+    CU(launch_orient((const uint64_t *)h->buf[h->cur], dwords, h->rows, h->words, h->transposed, false, g_stream));
     return GOL_OK;
 }
 
@@ -781,6 +827,9 @@ int many_plan(const gol_handle *hs, size_t n, size_t nwords, std::vector<CopyDes
         d[i].cur = scatter ? h->dev_cur : nullptr;
         d[i].offset = off;
         d[i].nwords = nw;
+        d[i].rows = h->rows;
+        d[i].words = h->words;
+        d[i].transposed = h->transposed;
         off += nw;
     }
     if ((size_t)off != nwords) return fail(GOL_EINVAL, "nwords = %zu, the boards hold %lld words", nwords, (long long)off);
@@ -837,7 +886,7 @@ int gol_get_region(gol_handle h, int64_t r0, int64_t c0, int64_t nr, int64_t nc,
     if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", n);
     if (h->layout == GOL_LAYOUT_PACKED)
         CU(launch_region_packed((const uint64_t *)h->buf[h->cur], h->rows, h->words, r0, c0, nr, nc,
-                                (uint8_t *)st.p, g_stream));
+                                (uint8_t *)st.p, h->transposed != 0, g_stream));
     else
         CU(launch_region_bytes((const uint8_t *)h->buf[h->cur], h->rows, h->cols, r0, c0, nr, nc,
                                (uint8_t *)st.p, g_stream));
@@ -953,6 +1002,10 @@ int gol_set_option(int key, int64_t v) {
             if (v < 1 || v > 3600000) return fail(GOL_EINVAL, "timeout out of range");
             g_opt_timeout_ms = v;
             return GOL_OK;
+        case GOL_OPT_ORIENTATION:
+            if (v < 0 || v > 2) return fail(GOL_EINVAL, "orientation must be 0, 1 or 2");
+            g_opt_orient = v;
+            return GOL_OK;
     }
     return fail(GOL_EINVAL, "unknown option %d", key);
 }
@@ -964,6 +1017,7 @@ int gol_get_option(int key, int64_t *v) {
         case GOL_OPT_TILE_ROWS: *v = g_opt_rows; return GOL_OK;
         case GOL_OPT_USE_GRAPHS: *v = g_opt_graphs; return GOL_OK;
         case GOL_OPT_WAIT_TIMEOUT_MS: *v = g_opt_timeout_ms; return GOL_OK;
+        case GOL_OPT_ORIENTATION: *v = g_opt_orient; return GOL_OK;
     }
     return fail(GOL_EINVAL, "unknown option %d", key);
 }

@@ -112,6 +112,10 @@ struct CopyDesc {
     int32_t *cur;       // scatter: reset to 0 (may be null)
     int64_t offset;
     int64_t nwords;
+    int64_t rows;       // board geometry in the interchange layout
+    int64_t words;
+    int32_t transposed; // board stored transposed (see gol_api.cu)
+    int32_t pad;
 };
 
 // Launchers (one translation unit per K).  Return cudaGetLastError().
@@ -129,7 +133,12 @@ cudaError_t launch_pack(const uint8_t *cells, uint64_t *words, int64_t R, int64_
 cudaError_t launch_check_bytes(const uint8_t *cells, int64_t n, int32_t *bad, cudaStream_t s);
 cudaError_t launch_unpack(const uint64_t *words, uint8_t *cells, int64_t R, int64_t W, cudaStream_t s);
 cudaError_t launch_region_packed(const uint64_t *words, int64_t R, int64_t W, int64_t r0, int64_t c0,
-                                 int64_t nr, int64_t nc, uint8_t *out, cudaStream_t s);
+                                 int64_t nr, int64_t nc, uint8_t *out, bool transposed, cudaStream_t s);
+// R x W interchange words <-> resident storage (the transpose when
+// `transposed`); to_res selects the direction.  src and dst must differ when
+// transposed.
+cudaError_t launch_orient(const uint64_t *src, uint64_t *dst, int64_t R, int64_t W, bool transposed, bool to_res,
+                          cudaStream_t s);
 cudaError_t launch_region_bytes(const uint8_t *cells, int64_t R, int64_t C, int64_t r0, int64_t c0,
                                 int64_t nr, int64_t nc, uint8_t *out, cudaStream_t s);
 cudaError_t launch_popcount_packed(const uint64_t *words, int64_t n, unsigned long long *out,

@@ -102,7 +102,7 @@ __global__ void pack_kernel(const uint8_t *__restrict__ cells, uint64_t *__restr
             }
         }
         if (any_high) atomicExch(bad, 1);
-        words[i] = to_resident(w);
+        words[i] = w;
     }
 }
 
@@ -116,7 +116,7 @@ __global__ void unpack_kernel(const uint64_t *__restrict__ words, uint8_t *__res
                               int64_t nwords) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t w = to_interchange(words[i]);
+        const uint64_t w = words[i];
         uint4 *p = reinterpret_cast<uint4 *>(cells + i * 64);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -137,13 +137,16 @@ __device__ __forceinline__ int64_t wrap(int64_t x, int64_t m) {
 
 __global__ void region_packed_kernel(const uint64_t *__restrict__ words, int64_t R, int64_t W,
                                      int64_t r0, int64_t c0, int64_t nr, int64_t nc,
-                                     uint8_t *__restrict__ out) {
+                                     uint8_t *__restrict__ out, bool transposed) {
     const int64_t n = nr * nc, C = W * 64;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t y = i / nc, x = i - y * nc;
         const int64_t r = wrap(r0 + y, R), c = wrap(c0 + x, C);
-        out[i] = (uint8_t)((words[r * W + (c >> 6)] >> resident_bit((int)(c & 63))) & 1u);
+        // transposed storage holds cell (r, c) at stored row c, stored column r
+        const int64_t sr = transposed ? c : r, sc = transposed ? r : c;
+        const int64_t sw = transposed ? R / 64 : W;
+        out[i] = (uint8_t)((words[sr * sw + (sc >> 6)] >> resident_bit((int)(sc & 63))) & 1u);
     }
 }
 
@@ -182,17 +185,83 @@ __global__ void convert_kernel(const uint64_t *src, uint64_t *dst, int64_t n, bo
     }
 }
 
+// One warp transposes the 64 x 64 cell tile whose rows are [64 ti, 64 ti + 64)
+// and whose columns are word tj of `src` (src_w words per row) into rows
+// [64 tj, 64 tj + 64), word ti of `dst` (dst_w words per row).  Bit j of
+// output row 64 tj + j's word is gathered from the 64 input rows with two
+// warp ballots.  from_res / to_res convert words from / to the resident layout.
+__device__ __forceinline__ void transpose_tile(const uint64_t *__restrict__ src, int64_t src_w, int64_t ti,
+                                               int64_t tj, uint64_t *__restrict__ dst, int64_t dst_w,
+                                               bool from_res, bool to_res) {
+    const int lane = threadIdx.x & 31;
+    uint64_t a = src[(64 * ti + lane) * src_w + tj];
+    uint64_t b = src[(64 * ti + 32 + lane) * src_w + tj];
+    if (from_res) {
+        a = to_interchange(a);
+        b = to_interchange(b);
+    }
+    uint64_t out_a = 0, out_b = 0;   // output rows 64 tj + lane and 64 tj + 32 + lane
+#pragma unroll 8
+    for (int j = 0; j < 64; ++j) {
+        const uint32_t lo = __ballot_sync(0xffffffffu, (uint32_t)(a >> j) & 1u);
+        const uint32_t hi = __ballot_sync(0xffffffffu, (uint32_t)(b >> j) & 1u);
+        const uint64_t w = (uint64_t)lo | ((uint64_t)hi << 32);
+        if (j == lane) out_a = w;
+        if (j == lane + 32) out_b = w;
+    }
+    if (to_res) {
+        out_a = to_resident(out_a);
+        out_b = to_resident(out_b);
+    }
+    dst[(64 * tj + lane) * dst_w + ti] = out_a;
+    dst[(64 * tj + 32 + lane) * dst_w + ti] = out_b;
+}
+
+// R x W interchange words -> resident storage: (64 W) x (R / 64) when
+// transposed, else R x W.  Reverse direction with to_res = false.
+__global__ void orient_kernel(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, int64_t R, int64_t W,
+                              bool transposed, bool to_res) {
+    if (!transposed) {
+        const int64_t n = R * W;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const uint64_t w = src[i];
+            dst[i] = to_res ? to_resident(w) : to_interchange(w);
+        }
+        return;
+    }
+    // to_res: src is the board (R rows, W words); dst the stored transpose.
+    // from resident: src is the stored transpose (64 W rows, R / 64 words).
+    const int64_t rows_t = to_res ? R / 64 : W, cols_t = to_res ? W : R / 64;
+    const int64_t src_w = to_res ? W : R / 64, dst_w = to_res ? R / 64 : W;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t t = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32; t < rows_t * cols_t; t += warps)
+        transpose_tile(src, src_w, t / cols_t, t % cols_t, dst, dst_w, !to_res, to_res);
+}
+
 // --- many boards <-> one contiguous staging buffer ----------------------------
 // block b copies the words of board b; a null `cur` is not written
 __global__ void scatter_boards_kernel(const CopyDesc *__restrict__ d, const uint64_t *__restrict__ staging) {
     const CopyDesc c = d[blockIdx.x];
-    for (int64_t i = threadIdx.x; i < c.nwords; i += blockDim.x) c.board[i] = to_resident(staging[c.offset + i]);
+    if (!c.transposed) {
+        for (int64_t i = threadIdx.x; i < c.nwords; i += blockDim.x) c.board[i] = to_resident(staging[c.offset + i]);
+    } else {
+        const int64_t tiles = (c.rows / 64) * c.words;
+        for (int64_t t = threadIdx.x / 32; t < tiles; t += blockDim.x / 32)
+            transpose_tile(staging + c.offset, c.words, t / c.words, t % c.words, c.board, c.rows / 64, false, true);
+    }
     if (threadIdx.x == 0 && c.cur) *c.cur = 0;
 }
 
 __global__ void gather_boards_kernel(const CopyDesc *__restrict__ d, uint64_t *__restrict__ staging) {
     const CopyDesc c = d[blockIdx.x];
-    for (int64_t i = threadIdx.x; i < c.nwords; i += blockDim.x) staging[c.offset + i] = to_interchange(c.board[i]);
+    if (!c.transposed) {
+        for (int64_t i = threadIdx.x; i < c.nwords; i += blockDim.x) staging[c.offset + i] = to_interchange(c.board[i]);
+    } else {
+        const int64_t rb = c.rows / 64, tiles = rb * c.words;
+        for (int64_t t = threadIdx.x / 32; t < tiles; t += blockDim.x / 32)
+            transpose_tile(c.board, rb, t / rb, t % rb, staging + c.offset, c.words, true, false);
+    }
 }
 
 // --- integer-pipe probe -------------------------------------------------------
@@ -257,8 +326,16 @@ cudaError_t launch_unpack(const uint64_t *words, uint8_t *cells, int64_t R, int6
 }
 
 cudaError_t launch_region_packed(const uint64_t *words, int64_t R, int64_t W, int64_t r0, int64_t c0,
-                                 int64_t nr, int64_t nc, uint8_t *out, cudaStream_t s) {
-    region_packed_kernel<<<grid_for(nr * nc), kBlock, 0, s>>>(words, R, W, r0, c0, nr, nc, out);
+                                 int64_t nr, int64_t nc, uint8_t *out, bool transposed, cudaStream_t s) {
+    region_packed_kernel<<<grid_for(nr * nc), kBlock, 0, s>>>(words, R, W, r0, c0, nr, nc, out, transposed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_orient(const uint64_t *src, uint64_t *dst, int64_t R, int64_t W, bool transposed, bool to_res,
+                          cudaStream_t s) {
+    if (R * W == 0) return cudaSuccess;
+    const int64_t work = transposed ? (R / 64) * W * 32 : R * W;   // threads
+    orient_kernel<<<grid_for(work, kBlock, 1 << 16), kBlock, 0, s>>>(src, dst, R, W, transposed, to_res);
     return cudaGetLastError();
 }
 

@@ -343,6 +343,13 @@ __device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pa
         }
     }
     __syncwarp();
+    if (ud.nnb == 0) {
+        // a unit with no neighbours (a board of one unit) depends on nobody
+        // but itself: run its next pass at once, without fences or a claim
+        if (pass >= npass) return -1;
+        if (lane == 0) A.claimed[u] = pass + 1;
+        return u;
+    }
     // Every completer orders its `done` store before its reads of the other
     // counters with a sequentially consistent fence: of two units finishing at
     // the same time, at least one sees the other's store.

@@ -37,6 +37,7 @@ GOL_OPT_GENS_PER_PASS = 1
 GOL_OPT_TILE_ROWS = 2
 GOL_OPT_USE_GRAPHS = 3
 GOL_OPT_WAIT_TIMEOUT_MS = 4
+GOL_OPT_ORIENTATION = 5
 
 # every symbol declared in include/gol.h
 EXPORTED = (

@@ -326,3 +326,62 @@ def test_many_board_transfers(gol):
         gol.gol_set_packed_batch(hs, flat[:-1])
     with pytest.raises(gol.GolError):
         gol.gol_set_packed_batch(hs + hs[:1], np.concatenate([flat, flat[:specs[0].rows * specs[0].cols // 64]]))
+
+
+@pytest.mark.parametrize("orient", [1, 2])
+def test_storage_orientation_all_io_paths(gol, orient):
+    # the same results whether the library stores the board as is (1) or
+    # transposed (2), through every way in and out of the device
+    import torch
+
+    gol.gol_set_option(gol.GOL_OPT_ORIENTATION, orient)
+    try:
+        shapes = [(64, 128), (128, 1216), (192, 64), (256, 2176), (64, 4096)]
+        for i, (R, C) in enumerate(shapes):
+            cells = synth.bernoulli_board(R, C, 0.45, 500 + i)
+            want = oracle.run(cells, 13)
+            for torus in (True, False):
+                want_t = want if torus else oracle.run(cells, 13, torus=False)
+                # bytes in, bytes out
+                b = gol.Board(R, C, torus=torus)
+                b.set(cells)
+                b.step(13)
+                assert_same(b.get(), want_t, "orient %d %dx%d torus=%s bytes" % (orient, R, C, torus))
+                # packed out, region, population
+                assert_same(oracle.unpack_words(b.get_packed()), want_t, "packed out")
+                reg = b.region(R - 5, C - 7, 11, 19)
+                assert_same(reg, want_t[np.ix_(np.arange(R - 5, R + 6) % R, np.arange(C - 7, C + 12) % C)], "region")
+                assert b.population() == oracle.population(want_t)
+                b.close()
+            # packed in, device in and out
+            b = gol.Board(R, C)
+            b.set_packed(synth.pack_cells(cells))
+            b.step(5)
+            dev = torch.empty(R * C // 64, dtype=torch.int64, device="cuda")
+            torch.cuda.synchronize()
+            gol.gol_get_packed_device(b.handle, dev.data_ptr(), dev.numel())
+            gol.gol_sync(b.handle)
+            got = dev.cpu().numpy().view(np.uint64).reshape(R, C // 64)
+            assert_same(oracle.unpack_words(got), oracle.run(cells, 5), "device out")
+            gol.gol_set_packed_device(b.handle, dev.data_ptr(), dev.numel())
+            b.step(8)
+            assert_same(b.get(), want, "device in")
+            b.close()
+        # many-board transfers
+        boards = [gol.Board(R, C) for R, C in shapes]
+        cells = [synth.bernoulli_board(R, C, 0.3, 900 + i) for i, (R, C) in enumerate(shapes)]
+        flat = np.concatenate([synth.pack_cells(c).reshape(-1) for c in cells])
+        hs = [b.handle for b in boards]
+        gol.gol_set_packed_batch(hs, flat)
+        gol.step_batch(boards, [7] * len(boards))
+        out = np.empty_like(flat)
+        gol.gol_get_packed_batch(hs, out)
+        off = 0
+        for (R, C), c in zip(shapes, cells):
+            n = R * C // 64
+            assert_same(oracle.unpack_words(out[off:off + n].reshape(R, C // 64)), oracle.run(c, 7), "batch io")
+            off += n
+        for b in boards:
+            b.close()
+    finally:
+        gol.gol_set_option(gol.GOL_OPT_ORIENTATION, 0)
