@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="batch", choices=["batch", "single", "bytes"])
+    ap.add_argument("--workload", default="batch",
+                    choices=["batch", "single", "huge", "bytes", "decomposition"])
     ap.add_argument("--boards", type=int, default=4096)
     ap.add_argument("--plain-sample", type=int, default=64, help="boards timed in the plain loop")
     ap.add_argument("--no-e2e", action="store_true")
@@ -227,6 +228,10 @@ def run_gpu(args, rank, world, local):
     elif args.workload == "single":
         specs = [synth.BoardSpec(0, 16384, 16384, 0.5, 10000, synth.SEED_SINGLE_16K)]
         workload = "single 16384x16384 toroidal packed board, Bernoulli(0.5), 10000 generations"
+    elif args.workload == "huge":
+        specs = [synth.BoardSpec(0, 131072, 131072, 0.5, 1000, synth.SEED_HUGE_128K)]
+        workload = ("single 131072x131072 toroidal packed board (2 GiB per buffer), Bernoulli(0.5) with a "
+                    "cleared 4096-row band holding a 64x64 glider lattice, 1000 generations")
     else:
         specs = [synth.BoardSpec(0, 256, 256, 0.3, 1000, synth.SEED_BYTES_256)]
         workload = "single 256x256 toroidal byte-per-cell board, Bernoulli(0.3), 1000 generations"
@@ -243,7 +248,9 @@ def run_gpu(args, rank, world, local):
         for s in specs:
             n = s.rows * s.cols // 64
             v = host[off:off + n].reshape(s.rows, s.cols // 64)
-            if s.density == 0.5:
+            if args.workload == "huge":
+                synth.glider_band_words(s.rows, s.cols // 64, s.seed, synth.GliderBand(), out=v)
+            elif s.density == 0.5:
                 synth.random_words(s.rows, s.cols // 64, s.seed, out=v)
             else:
                 v[:] = synth.bernoulli_words(s.rows, s.cols, s.density, s.seed)
@@ -384,6 +391,39 @@ def run_gpu(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_decomposition(args):
+    """The paper's Table 2 experiment on the host cores: the oracle's row,
+    column and block decompositions (Sections 2.1-2.2) timed at the table's
+    board shapes, iteration counts and thread counts."""
+    import oracle
+
+    oracle.build()
+    nproc = os.cpu_count() or 1
+    threads = sorted({t for t in (1, 2, 4, 8, nproc) if t <= nproc})
+    rows = []
+    for (R, C) in [(60, 120), (120, 240)]:
+        cells = synth.bernoulli_board(R, C, 0.3, 14408)
+        for iters in (500, 1000, 2000):
+            serial = None
+            for t in threads:
+                m = max(d for d in range(1, int(t ** 0.5) + 1) if t % d == 0)
+                for kind, fn in (("rows", lambda c: oracle.run_rows_omp(c, iters, t)),
+                                 ("cols", lambda c: oracle.run_cols_omp(c, iters, t)),
+                                 ("blocks", lambda c: oracle.run_blocks_omp(c, iters, m, t // m))):
+                    t0 = time.perf_counter()
+                    fn(cells)
+                    dt = time.perf_counter() - t0
+                    if serial is None:
+                        serial = dt
+                    rows.append({"board": "%dx%d" % (R, C), "iterations": iters, "threads": t,
+                                 "decomposition": kind, "seconds": round(dt, 4),
+                                 "speedup": round(serial / dt, 2),
+                                 "gcups": round(R * C * iters / dt / 1e9, 5)})
+    print(json.dumps({"metric": "host decomposition study (paper Table 2 shapes)", "cores": nproc,
+                      "data": "synthetic Bernoulli(0.3) boards; the paper's figure-3 pattern is not in the text",
+                      "rows": rows}), flush=True)
+
+
 def run_reference(args, rank, world):
     """The oracle on the host cores: each step a bounded sample of the workload."""
     if rank != 0:
@@ -428,6 +468,9 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "decomposition":
+        if rank == 0:
+            run_decomposition(args)
     else:
         run_gpu(args, rank, world, local)
 

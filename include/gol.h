@@ -183,12 +183,16 @@ const char *gol_last_error(void);
  *                          transposed when that fills the warps better,
  *                          1 = never transposed, 2 = always transposed.  The
  *                          interchange layout and every result are the same.
+ *   GOL_OPT_CHAIN_PERMILLE  planner bound on one board's chain of passes,
+ *                          in thousandths of the average work per warp slot
+ *                          (default 500); boards above it get shorter units
  * Unknown keys or values are GOL_EINVAL. */
 #define GOL_OPT_GENS_PER_PASS 1
 #define GOL_OPT_TILE_ROWS 2
 #define GOL_OPT_USE_GRAPHS 3
 #define GOL_OPT_WAIT_TIMEOUT_MS 4
 #define GOL_OPT_ORIENTATION 5
+#define GOL_OPT_CHAIN_PERMILLE 6
 int gol_set_option(int key, int64_t value);
 int gol_get_option(int key, int64_t *value);
 
@@ -199,6 +203,8 @@ int gol_get_option(int key, int64_t *value);
  * used. */
 int gol_tune_set(int64_t rows, int64_t cols, int gens_per_pass, int tile_rows);
 int gol_tune_get(int64_t rows, int64_t cols, int *gens_per_pass, int *tile_rows);
+/* Removes every entry of the autotune table (built-in defaults apply). */
+int gol_tune_reset(void);
 
 /* Device facts used for rooflines: SM count, L2 bytes, SM clock (kHz). */
 int gol_device_info(int *sm_count, int64_t *l2_bytes, int *sm_clock_khz);

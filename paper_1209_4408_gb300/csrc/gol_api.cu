@@ -74,6 +74,7 @@ void *(*g_alloc)(size_t, void *) = nullptr;
 void (*g_free)(void *, void *) = nullptr;
 void *g_alloc_ctx = nullptr;
 int64_t g_opt_k = 0, g_opt_rows = 0, g_opt_graphs = 1, g_opt_timeout_ms = 5000, g_opt_orient = 0;
+int64_t g_opt_chain = 500;   // chain cap, per mille of the average work per warp slot
 uint64_t g_serial = 0;
 
 struct DeviceState {
@@ -197,7 +198,7 @@ struct Plan {
     std::vector<uint64_t> serials;
     int K = 8;
     bool torus = true;
-    int64_t opt_k = 0, opt_rows = 0;
+    int64_t opt_k = 0, opt_rows = 0, opt_chain = 0;
     // host copies
     std::vector<BoardDesc> boards;
     std::vector<UnitDesc> units;
@@ -341,12 +342,23 @@ double lane_efficiency(int64_t rows, int64_t words, int K, int tile_rows) {
 }
 
 // Tile rows of a board with `npass` passes under a chain cap (see build_plan).
+// `chain_cap` bounds npass * H, the rows one unit streams through in all its
+// passes (halo rows left out), so that no board's chain of passes outlasts
+// the others' work.
 int capped_tile_rows(int rows, int64_t npass, int K, double chain_cap) {
-    if ((double)npass * (rows + 2 * K) > chain_cap) {
-        const int h = (int)(chain_cap / (double)npass) - 2 * K;
+    if ((double)npass * rows > chain_cap) {
+        const int h = (int)(chain_cap / (double)npass);
         rows = std::max(std::max(8, K), std::min(rows, h));
     }
     return rows;
+}
+
+// Halo-free row iterations of all passes of a board's units: each warp lane
+// segment streams ceil(R / S) rows per pass, for each of nt tiles.
+double board_row_work(int64_t srows, int64_t swords, int64_t npass) {
+    const int64_t S = swords <= 32 ? std::max<int64_t>(1, 32 / swords) : 1;
+    const int64_t nt = swords <= 32 ? 1 : (swords + kTileWords - 1) / kTileWords;
+    return (double)npass * (double)((srows + S - 1) / S) * (double)nt;
 }
 
 int build_plan(Plan &P) {
@@ -371,21 +383,17 @@ int build_plan(Plan &P) {
     const int64_t slots = (int64_t)g_dev.sms * std::max(1, bps) * kWarpsPerBlock;
     // Tile rows per board.  The tune table gives the tallest (most efficient)
     // unit; a board with many passes gets shorter units when its chain of
-    // passes, npass * (H + 2K) row iterations, would exceed half of the
-    // average work per warp slot, so that long runs do not set the makespan.
+    // passes would exceed a fraction (GOL_OPT_CHAIN_PERMILLE) of the average
+    // work per warp slot, so that long runs do not set the makespan and a
+    // single board is split into enough units for every warp.
     std::vector<int> hrows(n);
     double work = 0;
     for (size_t i = 0; i < n; ++i) {
         const gol_board *h = P.hs[i];
-        const int64_t np = (P.gens[i] + P.K - 1) / P.K;
         hrows[i] = std::max(1, tune_lookup(h->srows, h->swords * 64).rows);
-        const int W = (int)h->swords;
-        const int S = W <= 32 ? std::max(1, 32 / W) : 1;
-        const int nt = W <= 32 ? 1 : (W + kTileWords - 1) / kTileWords;
-        const double units = std::ceil((double)h->srows / ((double)S * hrows[i])) * nt;
-        work += units * np * (double)(hrows[i] + 2 * P.K);
+        work += board_row_work(h->srows, h->swords, (P.gens[i] + P.K - 1) / P.K);
     }
-    const double chain_cap = g_opt_rows ? 1e300 : 0.5 * work / (double)slots;
+    const double chain_cap = g_opt_rows ? 1e300 : (double)g_opt_chain / 1000.0 * work / (double)slots;
     for (size_t i = 0; i < n; ++i)
         hrows[i] = capped_tile_rows(hrows[i], (P.gens[i] + P.K - 1) / P.K, P.K, chain_cap);
     P.total_tasks = 0;
@@ -493,7 +501,8 @@ void clear_plans() {
 Plan *find_plan(const std::vector<gol_handle> &hs, const std::vector<int64_t> &gens, bool torus) {
     for (size_t i = 0; i < g_plans.size(); ++i) {
         Plan &P = *g_plans[i];
-        if (P.torus != torus || P.hs.size() != hs.size() || P.opt_k != g_opt_k || P.opt_rows != g_opt_rows)
+        if (P.torus != torus || P.hs.size() != hs.size() || P.opt_k != g_opt_k || P.opt_rows != g_opt_rows ||
+            P.opt_chain != g_opt_chain)
             continue;
         if (P.gens != gens || P.hs != hs) continue;
         bool same = true;
@@ -528,6 +537,7 @@ int run_packed(const std::vector<gol_handle> &hs, const std::vector<int64_t> &ge
         np->torus = torus;
         np->opt_k = g_opt_k;
         np->opt_rows = g_opt_rows;
+        np->opt_chain = g_opt_chain;
         for (auto h : hs) np->serials.push_back(h->serial);
         int rc = build_plan(*np);
         if (rc) return rc;
@@ -1006,6 +1016,10 @@ int gol_set_option(int key, int64_t v) {
             if (v < 0 || v > 2) return fail(GOL_EINVAL, "orientation must be 0, 1 or 2");
             g_opt_orient = v;
             return GOL_OK;
+        case GOL_OPT_CHAIN_PERMILLE:
+            if (v < 1 || v > 100000) return fail(GOL_EINVAL, "chain fraction out of range");
+            g_opt_chain = v;
+            return GOL_OK;
     }
     return fail(GOL_EINVAL, "unknown option %d", key);
 }
@@ -1018,6 +1032,7 @@ int gol_get_option(int key, int64_t *v) {
         case GOL_OPT_USE_GRAPHS: *v = g_opt_graphs; return GOL_OK;
         case GOL_OPT_WAIT_TIMEOUT_MS: *v = g_opt_timeout_ms; return GOL_OK;
         case GOL_OPT_ORIENTATION: *v = g_opt_orient; return GOL_OK;
+        case GOL_OPT_CHAIN_PERMILLE: *v = g_opt_chain; return GOL_OK;
     }
     return fail(GOL_EINVAL, "unknown option %d", key);
 }
@@ -1027,6 +1042,13 @@ int gol_tune_set(int64_t rows, int64_t cols, int k, int tile_rows) {
     if (rows < 1 || cols < 1 || !is_supported_k(k) || tile_rows < 1)
         return fail(GOL_EINVAL, "bad tune entry");
     g_tune[size_class(rows, cols)] = TuneEntry{k, tile_rows};
+    clear_plans();
+    return GOL_OK;
+}
+
+int gol_tune_reset(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tune.clear();
     clear_plans();
     return GOL_OK;
 }
@@ -1171,11 +1193,9 @@ extern "C" int gol_step_packed_noalloc(uint64_t *d_board, uint64_t *d_spare, int
     const int64_t slots = (int64_t)sms * std::max(1, bps) * kWarpsPerBlock;
     const int64_t npass_all = (generations + K - 1) / K;
     int h = std::max(1, te.rows);
-    {
-        const UnitGrid g0 = unit_grid(rows, W, K, h);
-        const double work = (double)g0.nb * g0.nt * npass_all * (h + 2 * K);
-        if (!g_opt_rows) h = capped_tile_rows(h, npass_all, K, 0.5 * work / (double)slots);
-    }
+    if (!g_opt_rows)
+        h = capped_tile_rows(h, npass_all, K,
+                             (double)g_opt_chain / 1000.0 * board_row_work(rows, W, npass_all) / (double)slots);
     UnitGrid g = unit_grid(rows, W, K, h);
     while (g.nb * g.nt > kStaticMaxUnits) {
         h = std::max(h + 1, (int)((int64_t)h * g.nb * g.nt / kStaticMaxUnits + 1));

@@ -38,6 +38,7 @@ GOL_OPT_TILE_ROWS = 2
 GOL_OPT_USE_GRAPHS = 3
 GOL_OPT_WAIT_TIMEOUT_MS = 4
 GOL_OPT_ORIENTATION = 5
+GOL_OPT_CHAIN_PERMILLE = 6
 
 # every symbol declared in include/gol.h
 EXPORTED = (
@@ -46,7 +47,7 @@ EXPORTED = (
     "gol_get_packed_batch", "gol_get_region",
     "gol_step", "gol_step_batch", "gol_population", "gol_generation", "gol_info", "gol_sync",
     "gol_set_stream", "gol_set_allocator", "gol_last_error", "gol_set_option", "gol_get_option",
-    "gol_tune_set", "gol_tune_get", "gol_device_info", "gol_probe_int_throughput",
+    "gol_tune_set", "gol_tune_get", "gol_tune_reset", "gol_device_info", "gol_probe_int_throughput",
     "gol_debug_unfilled_wait", "gol_step_packed_noalloc",
 )
 
@@ -99,6 +100,7 @@ def load() -> ctypes.CDLL:
         "gol_get_option": [i32, P(i64)],
         "gol_tune_set": [i64, i64, i32, i32],
         "gol_tune_get": [i64, i64, P(i32), P(i32)],
+        "gol_tune_reset": [],
         "gol_device_info": [P(i32), P(i64), P(i32)],
         "gol_probe_int_throughput": [P(ctypes.c_double), P(ctypes.c_double)],
         "gol_debug_unfilled_wait": [i64],
@@ -322,6 +324,10 @@ def gol_tune_get(rows: int, cols: int):
     k, t = ctypes.c_int(), ctypes.c_int()
     _check(load().gol_tune_get(rows, cols, ctypes.byref(k), ctypes.byref(t)))
     return k.value, t.value
+
+
+def gol_tune_reset():
+    _check(load().gol_tune_reset())
 
 
 def gol_device_info():
