@@ -185,7 +185,13 @@ const char *gol_last_error(void);
  *                          interchange layout and every result are the same.
  *   GOL_OPT_CHAIN_PERMILLE  planner bound on one board's chain of passes,
  *                          in thousandths of the average work per warp slot
- *                          (default 500); boards above it get shorter units
+ *                          (0 = 700 for one board, 500 for several); boards
+ *                          above it get shorter units
+ *   GOL_OPT_PIPELINE       0 = the step kernel shifts its three-row windows
+ *                          by register moves (fewer registers, more warps),
+ *                          1 = it rotates them by renaming (fewer issued
+ *                          instructions), -1 (default) = 1 for launches of
+ *                          several boards, 0 for one; results are identical
  * Unknown keys or values are GOL_EINVAL. */
 #define GOL_OPT_GENS_PER_PASS 1
 #define GOL_OPT_TILE_ROWS 2
@@ -193,6 +199,7 @@ const char *gol_last_error(void);
 #define GOL_OPT_WAIT_TIMEOUT_MS 4
 #define GOL_OPT_ORIENTATION 5
 #define GOL_OPT_CHAIN_PERMILLE 6
+#define GOL_OPT_PIPELINE 7
 int gol_set_option(int key, int64_t value);
 int gol_get_option(int key, int64_t *value);
 

@@ -11,3 +11,6 @@ from .gol import *  # noqa: F401,F403
 from .gol import load as _load
 
 _load()
+from . import autotune as _autotune  # noqa: E402
+
+_autotune.load_shipped()

@@ -23,6 +23,9 @@ DEFAULT_K = (2, 4, 8, 16)
 DEFAULT_ROWS = (8, 16, 32, 64, 128, 256)
 
 
+SHIPPED_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_gb300.json")
+
+
 def cache_path() -> str:
     return os.environ.get("GOL_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache",
                                                          "gol_gb300_tune.json"))
@@ -89,6 +92,11 @@ def load(path: str | None = None) -> int:
         gol.gol_tune_set(int(e["rows"]), int(e["cols"]), int(e["k"]), int(e["tile_rows"]))
         n += 1
     return n
+
+
+def load_shipped() -> int:
+    """Installs the table measured on a GB300 that ships with the package."""
+    return load(SHIPPED_TABLE)
 
 
 def tune_classes(shapes, gens: int = 256) -> list:

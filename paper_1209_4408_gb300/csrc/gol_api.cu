@@ -74,7 +74,8 @@ void *(*g_alloc)(size_t, void *) = nullptr;
 void (*g_free)(void *, void *) = nullptr;
 void *g_alloc_ctx = nullptr;
 int64_t g_opt_k = 0, g_opt_rows = 0, g_opt_graphs = 1, g_opt_timeout_ms = 5000, g_opt_orient = 0;
-int64_t g_opt_chain = 500;   // chain cap, per mille of the average work per warp slot
+int64_t g_opt_chain = 0;     // chain cap, per mille of the average work per warp slot (0 = auto)
+int64_t g_opt_variant = -1;  // step kernel variant (see launch_persistent), -1 = auto
 uint64_t g_serial = 0;
 
 struct DeviceState {
@@ -182,7 +183,7 @@ std::pair<int, int> size_class(int64_t rows, int64_t cols) {
 }
 TuneEntry tune_lookup(int64_t rows, int64_t cols) {
     auto it = g_tune.find(size_class(rows, cols));
-    TuneEntry t{6, 96};
+    TuneEntry t{6, 128};
     if (it != g_tune.end()) t = it->second;
     if (g_opt_k) t.k = (int)g_opt_k;
     if (g_opt_rows) t.rows = (int)g_opt_rows;
@@ -198,7 +199,8 @@ struct Plan {
     std::vector<uint64_t> serials;
     int K = 8;
     bool torus = true;
-    int64_t opt_k = 0, opt_rows = 0, opt_chain = 0;
+    int64_t opt_k = 0, opt_rows = 0, opt_chain = 0, opt_variant = 0;
+    int variant = 0;
     // host copies
     std::vector<BoardDesc> boards;
     std::vector<UnitDesc> units;
@@ -235,19 +237,26 @@ int supported_k(int k) {
         if (v <= k) s = v;
     return s;
 }
-cudaError_t occupancy_for(int K, bool torus, int *bps) {
+// Kernel variant of a plan: renaming rotation (1) measured faster on the
+// 4096-board batch, register moves (0) on a single 16384^2 board.
+int plan_variant(size_t nboards) {
+    if (g_opt_variant >= 0) return (int)g_opt_variant;
+    return nboards > 1 ? 1 : 0;
+}
+
+cudaError_t occupancy_for(int K, bool torus, int v, int *bps) {
     switch (K) {
 #define X(KV) \
-    case KV: return persistent_occupancy<KV>(torus, bps);
+    case KV: return persistent_occupancy<KV>(torus, v, bps);
         GOL_FOR_EACH_K(X)
 #undef X
     }
     return cudaErrorInvalidValue;
 }
-cudaError_t launch_for(int K, const PersistArgs &a, bool torus, int grid, cudaStream_t s) {
+cudaError_t launch_for(int K, const PersistArgs &a, bool torus, int variant, int grid, cudaStream_t s) {
     switch (K) {
 #define X(KV) \
-    case KV: return launch_persistent<KV>(a, torus, grid, s);
+    case KV: return launch_persistent<KV>(a, torus, variant, grid, s);
         GOL_FOR_EACH_K(X)
 #undef X
     }
@@ -353,6 +362,16 @@ int capped_tile_rows(int rows, int64_t npass, int K, double chain_cap) {
     return rows;
 }
 
+// Chain cap as a fraction of the average work per warp slot.  With one board
+// every unit has the same chain and the cap only sets the units per warp
+// (measured best near 0.7 on a 16384^2 board); with many boards of uneven
+// length a tighter cap keeps the longest chains off the critical path
+// (measured best near 0.5 on the 4096-board batch).
+double chain_fraction(size_t nboards) {
+    if (g_opt_chain > 0) return (double)g_opt_chain / 1000.0;
+    return nboards == 1 ? 0.7 : 0.5;
+}
+
 // Halo-free row iterations of all passes of a board's units: each warp lane
 // segment streams ceil(R / S) rows per pass, for each of nt tiles.
 double board_row_work(int64_t srows, int64_t swords, int64_t npass) {
@@ -377,8 +396,9 @@ int build_plan(Plan &P) {
         }
     }
     P.K = supported_k(std::max(1, K));
+    P.variant = plan_variant(n);
     int bps = 1;
-    cudaError_t e = occupancy_for(P.K, P.torus, &bps);
+    cudaError_t e = occupancy_for(P.K, P.torus, P.variant, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     const int64_t slots = (int64_t)g_dev.sms * std::max(1, bps) * kWarpsPerBlock;
     // Tile rows per board.  The tune table gives the tallest (most efficient)
@@ -393,7 +413,7 @@ int build_plan(Plan &P) {
         hrows[i] = std::max(1, tune_lookup(h->srows, h->swords * 64).rows);
         work += board_row_work(h->srows, h->swords, (P.gens[i] + P.K - 1) / P.K);
     }
-    const double chain_cap = g_opt_rows ? 1e300 : (double)g_opt_chain / 1000.0 * work / (double)slots;
+    const double chain_cap = g_opt_rows ? 1e300 : chain_fraction(n) * work / (double)slots;
     for (size_t i = 0; i < n; ++i)
         hrows[i] = capped_tile_rows(hrows[i], (P.gens[i] + P.K - 1) / P.K, P.K, chain_cap);
     P.total_tasks = 0;
@@ -451,7 +471,7 @@ int build_plan(Plan &P) {
 cudaError_t launch_plan_kernels(const Plan &P, cudaStream_t s) {
     cudaError_t e = launch_sched_init(P.args, (int)P.boards.size(), s);
     if (e != cudaSuccess) return e;
-    return launch_for(P.K, P.args, P.torus, P.grid, s);
+    return launch_for(P.K, P.args, P.torus, P.variant, P.grid, s);
 }
 
 // plan cache (most recently used first); evicted plans wait in the
@@ -502,7 +522,7 @@ Plan *find_plan(const std::vector<gol_handle> &hs, const std::vector<int64_t> &g
     for (size_t i = 0; i < g_plans.size(); ++i) {
         Plan &P = *g_plans[i];
         if (P.torus != torus || P.hs.size() != hs.size() || P.opt_k != g_opt_k || P.opt_rows != g_opt_rows ||
-            P.opt_chain != g_opt_chain)
+            P.opt_chain != g_opt_chain || P.opt_variant != g_opt_variant)
             continue;
         if (P.gens != gens || P.hs != hs) continue;
         bool same = true;
@@ -538,6 +558,8 @@ int run_packed(const std::vector<gol_handle> &hs, const std::vector<int64_t> &ge
         np->opt_k = g_opt_k;
         np->opt_rows = g_opt_rows;
         np->opt_chain = g_opt_chain;
+        np->opt_variant = g_opt_variant;
+
         for (auto h : hs) np->serials.push_back(h->serial);
         int rc = build_plan(*np);
         if (rc) return rc;
@@ -1017,8 +1039,12 @@ int gol_set_option(int key, int64_t v) {
             g_opt_orient = v;
             return GOL_OK;
         case GOL_OPT_CHAIN_PERMILLE:
-            if (v < 1 || v > 100000) return fail(GOL_EINVAL, "chain fraction out of range");
+            if (v < 0 || v > 100000) return fail(GOL_EINVAL, "chain fraction out of range");
             g_opt_chain = v;
+            return GOL_OK;
+        case GOL_OPT_PIPELINE:
+            if (v < -1 || v > 1) return fail(GOL_EINVAL, "pipeline variant must be -1, 0 or 1");
+            g_opt_variant = v;
             return GOL_OK;
     }
     return fail(GOL_EINVAL, "unknown option %d", key);
@@ -1033,6 +1059,7 @@ int gol_get_option(int key, int64_t *v) {
         case GOL_OPT_WAIT_TIMEOUT_MS: *v = g_opt_timeout_ms; return GOL_OK;
         case GOL_OPT_ORIENTATION: *v = g_opt_orient; return GOL_OK;
         case GOL_OPT_CHAIN_PERMILLE: *v = g_opt_chain; return GOL_OK;
+        case GOL_OPT_PIPELINE: *v = g_opt_variant; return GOL_OK;
     }
     return fail(GOL_EINVAL, "unknown option %d", key);
 }
@@ -1118,7 +1145,7 @@ int gol_debug_unfilled_wait(int64_t timeout_ms) {
     a.total_tasks = 1;   // ... but one ticket: its slot is never filled
     a.timeout_ns = timeout_ms * 1000000ll;
     CU(launch_sched_init(a, 0, g_stream));
-    CU(launch_persistent<1>(a, true, 1, g_stream));
+    CU(launch_persistent<1>(a, true, 0, 1, g_stream));
     CU(cudaStreamSynchronize(g_stream));
     int32_t status = 0;
     CU(cudaMemcpy(&status, a.ctr + 3, sizeof status, cudaMemcpyDeviceToHost));
@@ -1189,13 +1216,14 @@ extern "C" int gol_step_packed_noalloc(uint64_t *d_board, uint64_t *d_spare, int
     const TuneEntry te = tune_lookup(rows, cols);
     const int K = supported_k(std::max(1, te.k));
     int bps = 1;
-    CU(occupancy_for(K, torus != 0, &bps));
+    const int variant = plan_variant(1);
+    CU(occupancy_for(K, torus != 0, variant, &bps));
     const int64_t slots = (int64_t)sms * std::max(1, bps) * kWarpsPerBlock;
     const int64_t npass_all = (generations + K - 1) / K;
     int h = std::max(1, te.rows);
     if (!g_opt_rows)
         h = capped_tile_rows(h, npass_all, K,
-                             (double)g_opt_chain / 1000.0 * board_row_work(rows, W, npass_all) / (double)slots);
+                             chain_fraction(1) * board_row_work(rows, W, npass_all) / (double)slots);
     UnitGrid g = unit_grid(rows, W, K, h);
     while (g.nb * g.nt > kStaticMaxUnits) {
         h = std::max(h + 1, (int)((int64_t)h * g.nb * g.nt / kStaticMaxUnits + 1));
@@ -1238,7 +1266,7 @@ extern "C" int gol_step_packed_noalloc(uint64_t *d_board, uint64_t *d_spare, int
         CU(cudaMemcpyAsync(base, &bd, sizeof bd, cudaMemcpyHostToDevice, s));
         a.total_tasks = nunits * bd.npass;
         CU(launch_sched_init(a, 1, s));
-        CU(launch_for(K, a, torus != 0, grid, s));
+        CU(launch_for(K, a, torus != 0, variant, grid, s));
         cur ^= bd.npass & 1;
         left -= gens;
     }

@@ -119,10 +119,12 @@ struct CopyDesc {
 };
 
 // Launchers (one translation unit per K).  Return cudaGetLastError().
+// variant 0: window rows shift by register moves (fewer registers);
+// variant 1: window slots rotate by renaming (fewer issued instructions).
 template <int K>
-cudaError_t launch_persistent(const PersistArgs &a, bool torus, int grid, cudaStream_t s);
+cudaError_t launch_persistent(const PersistArgs &a, bool torus, int variant, int grid, cudaStream_t s);
 template <int K>
-cudaError_t persistent_occupancy(bool torus, int *blocks_per_sm);
+cudaError_t persistent_occupancy(bool torus, int variant, int *blocks_per_sm);
 
 // Utility kernels (kernels_util.cu).
 cudaError_t launch_sched_init(const PersistArgs &a, int nboards, cudaStream_t s);

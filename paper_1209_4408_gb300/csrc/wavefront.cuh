@@ -106,8 +106,10 @@ __device__ __forceinline__ void st_u64(uint64_t *p, uint32_t lo, uint32_t hi) {
 // ---------------------------------------------------------------------------
 // One pass of one unit by one warp.
 // ---------------------------------------------------------------------------
+// Variant of run_unit_pass whose three-row window shifts by register moves
+// (iteration loop unrolled twice); fewer registers, more issue slots.
 template <int K, bool TORUS, bool PARTIAL>
-__device__ __forceinline__ void run_unit_pass(const BoardDesc &bd, const UnitDesc &ud,
+__device__ __forceinline__ void run_unit_pass_moves(const BoardDesc &bd, const UnitDesc &ud,
                                               const uint64_t *__restrict__ src,
                                               uint64_t *__restrict__ dst, int kk) {
     constexpr unsigned kFull = 0xffffffffu;
@@ -270,6 +272,184 @@ __device__ __forceinline__ void run_unit_pass(const BoardDesc &bd, const UnitDes
     }
 }
 
+
+// Variant whose window slots rotate by renaming (loop unrolled three times).
+template <int K, bool TORUS, bool PARTIAL>
+__device__ __forceinline__ void run_unit_pass(const BoardDesc &bd, const UnitDesc &ud,
+                                              const uint64_t *__restrict__ src,
+                                              uint64_t *__restrict__ dst, int kk) {
+    constexpr unsigned kFull = 0xffffffffu;
+    constexpr int NPRO = 2 * K;                    // iterations before the first output row
+    constexpr int NPRO3 = (NPRO + 2) / 3 * 3;      // guarded iterations (multiple of 3)
+    const int lane = threadIdx.x & 31;
+    const int R = bd.R, W = bd.W;
+
+    // ---- lane geometry -------------------------------------------------
+    int seg = 0, word = 0, west_src = lane, east_src = lane;
+    bool loads = false, stores = false;
+    uint32_t west_mask = ~0u, east_mask = ~0u, lane_mask = ~0u;
+    if (ud.mode == kUnitFull) {
+        seg = lane / W;
+        word = lane - seg * W;
+        if (seg < ud.S) {
+            loads = stores = true;
+            const int base = lane - word;
+            west_src = base + (word == 0 ? W - 1 : word - 1);
+            east_src = base + (word == W - 1 ? 0 : word + 1);
+            if (!TORUS) {
+                if (word == 0) west_mask = 0;
+                if (word == W - 1) east_mask = 0;
+            }
+        } else {
+            seg = 0;
+            word = 0;
+        }
+    } else {
+        int w = ud.w0 - 1 + lane;
+        loads = lane < ud.U + 2;
+        stores = lane >= 1 && lane <= ud.U;
+        if (TORUS) {
+            w = w < 0 ? w + W : (w >= W ? w - W : w);
+        } else if (w < 0 || w >= W) {
+            lane_mask = 0;
+            loads = false;
+            w = 0;
+        }
+        word = loads ? w : 0;
+        west_src = lane == 0 ? 0 : lane - 1;
+        east_src = lane == 31 ? 31 : lane + 1;
+    }
+    const int a = ud.r0 + seg * ud.H;                       // first output row of the segment
+    const int seg_end = min(a + ud.H, ud.r_end);            // one past its last output row
+    const int nmain = ud.H;                                 // main-loop iterations
+
+    // ---- input row stream: row (a - K + j) of src ---------------------
+    int lrow = a - K;                                       // row of the next load (unwrapped)
+    int lwrap = lrow;                                       // wrapped row
+    if (TORUS) {
+        lwrap %= R;
+        if (lwrap < 0) lwrap += R;
+    }
+    const uint64_t *colp = src + word;
+    auto load_next = [&](uint32_t &lo, uint32_t &hi) {
+        lo = hi = 0;
+        if (TORUS) {
+            if (loads) {
+                const uint2 v = ld_cg_u64(colp + (size_t)lwrap * W);
+                lo = v.x;
+                hi = v.y;
+            }
+            if (++lwrap == R) lwrap = 0;
+        } else {
+            if (loads && lrow >= 0 && lrow < R) {
+                const uint2 v = ld_cg_u64(colp + (size_t)lrow * W);
+                lo = v.x;
+                hi = v.y;
+            }
+        }
+        ++lrow;
+    };
+
+    // ---- pipeline registers ----------------------------------------------
+    // Each stage keeps three row slots (row-sum planes and alive word) that
+    // take the roles (two rows back, one row back, current row) in turn: the
+    // iteration loop is unrolled three times so that the roles rotate by
+    // renaming instead of register moves.
+    uint32_t s0l[3][K], s0h[3][K], s1l[3][K], s1h[3][K], sal[3][K], sah[3][K];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int g = 0; g < K; ++g) s0l[r][g] = s0h[r][g] = s1l[r][g] = s1h[r][g] = sal[r][g] = sah[r][g] = 0;
+    uint32_t fl[3], fh[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) load_next(fl[u], fh[u]);
+
+    // One iteration: the gen-0 row (a - K + j) enters stage 0; returns the
+    // generation-kk row (a + j - 2K) leaving the last stage.  PH = j mod 3
+    // names the slot of the oldest row.  In the prologue (GUARD) stage g only
+    // runs once its window holds valid rows.
+    auto iterate = [&](uint32_t xl, uint32_t xh, int j, auto guard_tag, auto phase_tag) {
+        constexpr bool GUARD = decltype(guard_tag)::value;
+        constexpr int O = decltype(phase_tag)::value, M = (O + 1) % 3, N = (O + 2) % 3;
+        const int jr = a - K + j;
+#pragma unroll
+        for (int g = 0; g < K; ++g) {
+            if (GUARD && j < 2 * g) break;                  // input of stage g not produced yet
+            const uint32_t wh = __shfl_sync(kFull, xh, west_src) & west_mask;
+            const uint32_t el = __shfl_sync(kFull, xl, east_src) & east_mask;
+            // even columns (low half): west = odd column to the left = the
+            // high half shifted up by one, its bit 0 from the west word;
+            // east = the odd column to the right = the high half as is.
+            // odd columns (high half): west = the low half as is; east = the
+            // low half shifted down by one, its bit 31 from the east word.
+            const uint32_t Wl = __funnelshift_l(wh, xh, 1);
+            const uint32_t Eh = __funnelshift_r(xl, el, 1);
+            s0l[N][g] = lop3<kXor3>(Wl, xl, xh);
+            s0h[N][g] = lop3<kXor3>(xl, xh, Eh);
+            s1l[N][g] = lop3<kMaj3>(Wl, xl, xh);
+            s1h[N][g] = lop3<kMaj3>(xl, xh, Eh);
+            sal[N][g] = xl;
+            sah[N][g] = xh;
+            uint32_t ol = 0, oh = 0;
+            if (!GUARD || j >= 2 * g + 2) {
+                ol = rule32(s0l[O][g], s1l[O][g], s0l[M][g], s1l[M][g], s0l[N][g], s1l[N][g], sal[M][g]);
+                oh = rule32(s0h[O][g], s1h[O][g], s0h[M][g], s1h[M][g], s0h[N][g], s1h[N][g], sah[M][g]);
+                if (PARTIAL && g >= kk) {                   // pass shorter than K: identity stage
+                    ol = sal[M][g];
+                    oh = sah[M][g];
+                }
+                if (!TORUS) {
+                    const bool inside = (unsigned)(jr - g - 1) < (unsigned)R;
+                    ol = inside ? (ol & lane_mask) : 0u;
+                    oh = inside ? (oh & lane_mask) : 0u;
+                }
+            }
+            xl = ol;
+            xh = oh;
+        }
+        return make_uint2(xl, xh);
+    };
+
+    using P0 = std::integral_constant<int, 0>;
+    using P1 = std::integral_constant<int, 1>;
+    using P2 = std::integral_constant<int, 2>;
+    int orow = a;                                           // row of the next output
+    uint64_t *outp = dst + word;
+    auto emit = [&](uint2 o) {
+        if (stores && orow < seg_end) st_u64(outp + (size_t)orow * W, o.x, o.y);
+        ++orow;
+    };
+    // prologue: the first 2K iterations (rounded up to a multiple of 3) with
+    // guards; iterations from 2K on already produce output rows
+#pragma unroll 1
+    for (int j0 = 0; j0 < NPRO3; j0 += 3) {
+        uint32_t xl = fl[0], xh = fh[0];
+        load_next(fl[0], fh[0]);
+        uint2 o = iterate(xl, xh, j0, std::true_type{}, P0{});
+        if (j0 >= NPRO) emit(o);
+        xl = fl[1], xh = fh[1];
+        load_next(fl[1], fh[1]);
+        o = iterate(xl, xh, j0 + 1, std::true_type{}, P1{});
+        if (j0 + 1 >= NPRO) emit(o);
+        xl = fl[2], xh = fh[2];
+        load_next(fl[2], fh[2]);
+        o = iterate(xl, xh, j0 + 2, std::true_type{}, P2{});
+        if (j0 + 2 >= NPRO) emit(o);
+    }
+#pragma unroll 1
+    for (int j0 = NPRO3; j0 < NPRO + nmain; j0 += 3) {
+        uint32_t xl = fl[0], xh = fh[0];
+        load_next(fl[0], fh[0]);
+        emit(iterate(xl, xh, j0, std::false_type{}, P0{}));
+        xl = fl[1], xh = fh[1];
+        load_next(fl[1], fh[1]);
+        emit(iterate(xl, xh, j0 + 1, std::false_type{}, P1{}));
+        xl = fl[2], xh = fh[2];
+        load_next(fl[2], fh[2]);
+        emit(iterate(xl, xh, j0 + 2, std::false_type{}, P2{}));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Scheduler
 // ---------------------------------------------------------------------------
@@ -380,7 +560,7 @@ __device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pa
     return next;
 }
 
-template <int K, bool TORUS>
+template <int K, bool TORUS, int VARIANT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 persistent_step_kernel(const PersistArgs A) {
     constexpr unsigned kFull = 0xffffffffu;
@@ -410,10 +590,17 @@ persistent_step_kernel(const PersistArgs A) {
         const uint64_t *src = bd.buf[(cur + pass - 1) & 1];
         uint64_t *dst = bd.buf[(cur + pass) & 1];
         const int kk = pass_gens(bd, pass);
-        if (kk == K)
-            run_unit_pass<K, TORUS, false>(bd, ud, src, dst, K);
-        else
-            run_unit_pass<K, TORUS, true>(bd, ud, src, dst, kk);
+        if (VARIANT == 0) {
+            if (kk == K)
+                run_unit_pass_moves<K, TORUS, false>(bd, ud, src, dst, K);
+            else
+                run_unit_pass_moves<K, TORUS, true>(bd, ud, src, dst, kk);
+        } else {
+            if (kk == K)
+                run_unit_pass<K, TORUS, false>(bd, ud, src, dst, K);
+            else
+                run_unit_pass<K, TORUS, true>(bd, ud, src, dst, kk);
+        }
         __threadfence();
         __syncwarp();
         u = complete_pass(A, u, pass, ud, bd);
@@ -421,31 +608,40 @@ persistent_step_kernel(const PersistArgs A) {
 }
 
 template <int K>
-cudaError_t launch_persistent_impl(const PersistArgs &a, bool torus, int grid, cudaStream_t s) {
-    if (torus)
-        persistent_step_kernel<K, true><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
-    else
-        persistent_step_kernel<K, false><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+cudaError_t launch_persistent_impl(const PersistArgs &a, bool torus, int variant, int grid, cudaStream_t s) {
+    if (variant == 0) {
+        if (torus)
+            persistent_step_kernel<K, true, 0><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+        else
+            persistent_step_kernel<K, false, 0><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+    } else {
+        if (torus)
+            persistent_step_kernel<K, true, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+        else
+            persistent_step_kernel<K, false, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
 template <int K>
-cudaError_t persistent_occupancy_impl(bool torus, int *bps) {
-    if (torus)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true>,
-                                                             kWarpsPerBlock * 32, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false>,
-                                                         kWarpsPerBlock * 32, 0);
+cudaError_t persistent_occupancy_impl(bool torus, int variant, int *bps) {
+    const int t = kWarpsPerBlock * 32;
+    if (variant == 0)
+        return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, 0>, t, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, 0>, t, 0);
+    return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, 1>, t, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, 1>, t, 0);
 }
 
-#define GOL_INSTANTIATE_PERSISTENT(KV)                                                          \
-    template <>                                                                                 \
-    cudaError_t launch_persistent<KV>(const PersistArgs &a, bool torus, int grid, cudaStream_t s) { \
-        return launch_persistent_impl<KV>(a, torus, grid, s);                                   \
-    }                                                                                           \
-    template <>                                                                                 \
-    cudaError_t persistent_occupancy<KV>(bool torus, int *bps) {                                \
-        return persistent_occupancy_impl<KV>(torus, bps);                                       \
+#define GOL_INSTANTIATE_PERSISTENT(KV)                                                             \
+    template <>                                                                                    \
+    cudaError_t launch_persistent<KV>(const PersistArgs &a, bool torus, int variant, int grid,     \
+                                      cudaStream_t s) {                                            \
+        return launch_persistent_impl<KV>(a, torus, variant, grid, s);                             \
+    }                                                                                              \
+    template <>                                                                                    \
+    cudaError_t persistent_occupancy<KV>(bool torus, int variant, int *bps) {                      \
+        return persistent_occupancy_impl<KV>(torus, variant, bps);                                 \
     }
 
 }  // namespace gol

@@ -133,14 +133,23 @@ def test_packed_random_shapes(gol, opts, R, C, torus):
                         "%dx%d torus=%s K=%d rows=%d gens=%d" % (R, C, torus, k, rows, gens))
 
 
-@pytest.mark.parametrize("k", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 8, 16])
 @pytest.mark.parametrize("rows", [1, 8, 64, 1000])
-def test_packed_result_independent_of_pass_and_tile(gol, opts, k, rows):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_packed_result_independent_of_pass_and_tile(gol, opts, k, rows, variant):
     R, C, G = 192, 2240, 23
     cells = synth.bernoulli_board(R, C, 0.5, 4242)
     want = oracle.run(cells, G)
     opts(k, rows)
-    assert_same(run_gpu(gol, cells, G), want, "K=%d rows=%d" % (k, rows))
+    gol.gol_set_option(gol.GOL_OPT_PIPELINE, variant)
+    try:
+        assert_same(run_gpu(gol, cells, G), want, "K=%d rows=%d variant=%d" % (k, rows, variant))
+        # bounded board and a board narrow enough for several lane segments
+        cells2 = synth.bernoulli_board(130, 320, 0.4, 77)
+        assert_same(run_gpu(gol, cells2, G, torus=False), oracle.run(cells2, G, torus=False),
+                    "bounded K=%d rows=%d variant=%d" % (k, rows, variant))
+    finally:
+        gol.gol_set_option(gol.GOL_OPT_PIPELINE, 0)
 
 
 def test_packed_split_runs_compose(gol):
