@@ -59,6 +59,29 @@ def parse():
     return ap.parse_args()
 
 
+PROFILE = os.path.join(ROOT, "profiles", "persistent_step_kernel.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_1209_4408_gb300", "csrc", "wavefront.cuh")
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per launch of the step kernel for `workload` as captured by
+    ncu (dram__bytes_read.sum + dram__bytes_write.sum), or None when no
+    capture was taken of the kernel source as it is now."""
+    import hashlib
+
+    try:
+        sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+        for ln in open(PROFILE):
+            parts = ln.split()
+            # "traffic <workload> <bytes> sha256 <hash>"
+            if len(parts) == 5 and parts[0] == "traffic" and parts[1] == workload and parts[3] == "sha256":
+                if parts[4] == sha:
+                    return int(parts[2])
+    except OSError:
+        return None
+    return None
+
+
 def rank_batch(specs, rank: int):
     """Weak scaling: every rank steps its own copy of the batch; rank r > 0
     draws its boards from seeds derived from the rank."""
@@ -350,7 +373,9 @@ def run_gpu(args, rank, world, local):
     if achieved_tops is not None:
         peak = ops / 1e12
         roofline = {"bound": "alu", "achieved": round(achieved_tops, 3), "peak": round(peak, 3),
-                    "unit": "Tops/s", "frac": round(achieved_tops / peak, 4), "traffic": None,
+                    "unit": "Tops/s", "frac": round(achieved_tops / peak, 4),
+                    "traffic": recorded_traffic(args.workload) if args.boards == 4096 or args.workload != "batch"
+                    else None,
                     "peak_source": "integer-pipe probe (LOP3/funnel-shift mix) measured in this run",
                     "algorithmic_ops_per_launch": total_words_gens * INT_OPS_PER_WORD_GEN}
 

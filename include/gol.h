@@ -144,6 +144,11 @@ int gol_step_batch(const gol_handle *hs, const int64_t *generations, size_t n);
  * Synchronous. */
 int gol_population(gol_handle h, uint64_t *out);
 
+/* Population trajectory (the form of the paper's Table 1): advances the
+ * board n times by `every` generations (every >= 1) and writes the number of
+ * live cells after each advance to host out[0..n).  Synchronous. */
+int gol_population_trace(gol_handle h, int64_t every, size_t n, uint64_t *out);
+
 /* Generations applied since the last gol_set / gol_set_packed. */
 int gol_generation(gol_handle h, int64_t *out);
 

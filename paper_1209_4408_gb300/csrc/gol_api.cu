@@ -417,7 +417,18 @@ int build_plan(Plan &P) {
     for (size_t i = 0; i < n; ++i)
         hrows[i] = capped_tile_rows(hrows[i], (P.gens[i] + P.K - 1) / P.K, P.K, chain_cap);
     P.total_tasks = 0;
-    for (size_t i = 0; i < n; ++i) {
+    P.boards.resize(n);
+    P.npass.resize(n);
+    // Units are numbered, and so queued at launch, longest chain of passes
+    // first (npass * H): the boards that finish last start first.
+    std::vector<size_t> order(n);
+    for (size_t i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        const double cx = (double)((P.gens[x] + P.K - 1) / P.K) * hrows[x];
+        const double cy = (double)((P.gens[y] + P.K - 1) / P.K) * hrows[y];
+        return cx > cy;
+    });
+    for (size_t i : order) {
         gol_board *h = P.hs[i];
         BoardDesc bd{};
         bd.buf[0] = (uint64_t *)h->buf[0];
@@ -429,8 +440,8 @@ int build_plan(Plan &P) {
         bd.npass = (int32_t)((P.gens[i] + P.K - 1) / P.K);
         build_units(h, (int)i, P.K, hrows[i], P.units, &bd.nunits);
         P.total_tasks += (int64_t)bd.nunits * bd.npass;
-        P.boards.push_back(bd);
-        P.npass.push_back(bd.npass);
+        P.boards[i] = bd;
+        P.npass[i] = bd.npass;
     }
     if (P.total_tasks >= (int64_t(1) << 31) || P.units.size() >= (size_t(1) << 30))
         return fail(GOL_EINVAL, "batch too large for one launch (%lld tasks)", (long long)P.total_tasks);
@@ -932,8 +943,38 @@ int gol_step(gol_handle h, int64_t generations) {
     return gol_step_batch(hs, gs, 1);
 }
 
+namespace {
+int step_batch_locked(const gol_handle *hs, const int64_t *generations, size_t n);
+}
+
 int gol_step_batch(const gol_handle *hs, const int64_t *generations, size_t n) {
     std::lock_guard<std::mutex> lk(g_mu);
+    return step_batch_locked(hs, generations, n);
+}
+
+int gol_population_trace(gol_handle h, int64_t every, size_t n, uint64_t *out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!valid(h) || (!out && n)) return fail(GOL_EINVAL, "invalid handle or null output");
+    if (every < 1) return fail(GOL_EINVAL, "every must be >= 1");
+    if (n == 0) return GOL_OK;
+    Scratch st(n * sizeof(unsigned long long));
+    if (!st.p) return fail(GOL_ENOMEM, "population trace scratch");
+    unsigned long long *slots = (unsigned long long *)st.p;
+    CU(cudaMemsetAsync(slots, 0, n * sizeof(unsigned long long), g_stream));
+    for (size_t i = 0; i < n; ++i) {
+        int rc = step_batch_locked(&h, &every, 1);
+        if (rc) return rc;
+        if (h->layout == GOL_LAYOUT_PACKED)
+            CU(launch_popcount_packed((const uint64_t *)h->buf[h->cur], h->rows * h->words, slots + i, g_stream));
+        else
+            CU(launch_popcount_bytes((const uint8_t *)h->buf[h->cur], h->rows * h->cols, slots + i, g_stream));
+    }
+    CU(cudaMemcpyAsync(out, slots, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, g_stream));
+    return sync_stream();
+}
+
+namespace {
+int step_batch_locked(const gol_handle *hs, const int64_t *generations, size_t n) {
     if (n == 0) return GOL_OK;
     if (!hs || !generations) return fail(GOL_EINVAL, "null arrays");
     std::unordered_set<gol_handle> seen;
@@ -982,6 +1023,7 @@ int gol_step_batch(const gol_handle *hs, const int64_t *generations, size_t n) {
     }
     return GOL_OK;
 }
+}  // namespace
 
 int gol_population(gol_handle h, uint64_t *out) {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -601,7 +601,9 @@ persistent_step_kernel(const PersistArgs A) {
             else
                 run_unit_pass<K, TORUS, true>(bd, ud, src, dst, kk);
         }
-        __threadfence();
+        // every lane's stores of this pass are ordered before lane 0's
+        // release of done[u] (acquire-release fence, then the warp barrier)
+        fence_acq_rel_gpu();
         __syncwarp();
         u = complete_pass(A, u, pass, ud, bd);
     }

@@ -46,7 +46,8 @@ EXPORTED = (
     "gol_create", "gol_create_ex", "gol_destroy", "gol_set", "gol_get", "gol_set_packed",
     "gol_get_packed", "gol_set_packed_device", "gol_get_packed_device", "gol_set_packed_batch",
     "gol_get_packed_batch", "gol_get_region",
-    "gol_step", "gol_step_batch", "gol_population", "gol_generation", "gol_info", "gol_sync",
+    "gol_step", "gol_step_batch", "gol_population", "gol_population_trace", "gol_generation", "gol_info",
+    "gol_sync",
     "gol_set_stream", "gol_set_allocator", "gol_last_error", "gol_set_option", "gol_get_option",
     "gol_tune_set", "gol_tune_get", "gol_tune_reset", "gol_device_info", "gol_probe_int_throughput",
     "gol_debug_unfilled_wait", "gol_step_packed_noalloc",
@@ -91,6 +92,7 @@ def load() -> ctypes.CDLL:
         "gol_step": [vp, i64],
         "gol_step_batch": [vp, vp, sz],
         "gol_population": [vp, P(ctypes.c_uint64)],
+        "gol_population_trace": [vp, i64, sz, vp],
         "gol_generation": [vp, P(i64)],
         "gol_info": [vp, P(i64), P(i64), P(i32), P(i32)],
         "gol_sync": [vp],
@@ -236,6 +238,12 @@ def gol_population(h: int) -> int:
     v = ctypes.c_uint64()
     _check(load().gol_population(h, ctypes.byref(v)))
     return v.value
+
+
+def gol_population_trace(h: int, every: int, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.uint64)
+    _check(load().gol_population_trace(h, int(every), int(n), _ptr(out) if n else None))
+    return out
 
 
 def gol_generation(h: int) -> int:

@@ -394,3 +394,21 @@ def test_storage_orientation_all_io_paths(gol, orient):
             b.close()
     finally:
         gol.gol_set_option(gol.GOL_OPT_ORIENTATION, 0)
+
+
+@pytest.mark.parametrize("layout", [1, 2])
+def test_population_trace(gol, layout):
+    # populations after every 7 generations, the form of the paper's Table 1
+    R, C = 96, 192
+    cells = synth.bernoulli_board(R, C, 0.35, 61)
+    b = gol.Board(R, C, layout=layout)
+    b.set(cells)
+    got = gol.gol_population_trace(b.handle, 7, 12)
+    x, want = cells, []
+    for _ in range(12):
+        x = oracle.run(x, 7)
+        want.append(oracle.population(x))
+    assert [int(v) for v in got] == want
+    assert b.generation() == 84
+    assert_same(b.get(), x, "after the trace")
+    b.close()
