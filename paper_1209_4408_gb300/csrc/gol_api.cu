@@ -36,6 +36,9 @@ struct gol_board {
     // board's own rows x words.
     int transposed = 0;
     int64_t srows = 0, swords = 0;
+    // byte boards: captured graphs of 64 generations, per starting buffer
+    cudaGraphExec_t byte_graph[2] = {nullptr, nullptr};
+    cudaStream_t byte_graph_stream = nullptr;
 };
 
 namespace {
@@ -615,7 +618,44 @@ int run_packed(const std::vector<gol_handle> &hs, const std::vector<int64_t> &ge
     return GOL_OK;
 }
 
+// Byte boards: one launch per generation.  Long runs on a non-default stream
+// replay a captured CUDA graph of kByteGraphGens launches (an even number,
+// so the current buffer is the same before and after a replay); one graph per
+// starting buffer is kept with the board.
+constexpr int kByteGraphGens = 64;
+
 int step_bytes(gol_handle h, int64_t G) {
+    if (g_opt_graphs && g_stream != nullptr && G >= 2 * kByteGraphGens) {
+        if (h->byte_graph_stream != g_stream) {
+            for (auto &ge : h->byte_graph)
+                if (ge) {
+                    cudaGraphExecDestroy(ge);
+                    ge = nullptr;
+                }
+            h->byte_graph_stream = g_stream;
+        }
+        cudaGraphExec_t &ge = h->byte_graph[h->cur];
+        if (!ge) {
+            cudaGraph_t graph = nullptr;
+            CU(cudaStreamBeginCapture(g_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int g = 0; g < kByteGraphGens && e == cudaSuccess; ++g) {
+                const int c = h->cur ^ (g & 1);
+                e = launch_byte_step((const uint8_t *)h->buf[c], (uint8_t *)h->buf[c ^ 1], h->rows, h->cols,
+                                     h->torus, g_stream);
+            }
+            cudaError_t e2 = cudaStreamEndCapture(g_stream, &graph);
+            if (e != cudaSuccess) return cuda_fail(e, "capturing byte steps");
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ge, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        for (; G >= kByteGraphGens; G -= kByteGraphGens) {
+            CU(cudaGraphLaunch(ge, g_stream));
+            h->generation += kByteGraphGens;
+        }
+    }
     for (int64_t g = 0; g < G; ++g) {
         const uint8_t *in = (const uint8_t *)h->buf[h->cur];
         uint8_t *out = (uint8_t *)h->buf[h->cur ^ 1];
@@ -734,6 +774,8 @@ int gol_destroy(gol_handle h) {
     if (!valid(h)) return fail(GOL_EINVAL, "invalid handle");
     drop_plans_of(h);
     cudaStreamSynchronize(g_stream);
+    for (auto ge : h->byte_graph)
+        if (ge) cudaGraphExecDestroy(ge);
     dev_free(h->buf[0], h->free_fn, h->alloc_ctx);
     dev_free(h->buf[1], h->free_fn, h->alloc_ctx);
     dev_free(h->dev_cur, h->free_fn, h->alloc_ctx);

@@ -412,3 +412,24 @@ def test_population_trace(gol, layout):
     assert b.generation() == 84
     assert_same(b.get(), x, "after the trace")
     b.close()
+
+
+def test_bytes_graph_replay_on_torch_stream(gol):
+    # long byte-board runs on a non-default stream replay a captured graph of
+    # 64 generations; results match the oracle from either starting buffer
+    import torch
+
+    stream = torch.cuda.Stream()
+    gol.gol_set_stream(stream)
+    try:
+        cells = synth.bernoulli_board(100, 130, 0.35, 2)
+        b = gol.Board(100, 130, layout=gol.GOL_LAYOUT_BYTES)
+        b.set(cells)
+        b.step(1)            # start the replays from the second buffer
+        b.step(300)          # 4 replays + 44 single launches
+        b.step(129)
+        assert_same(b.get(), oracle.run(cells, 430), "byte graph replays")
+        assert b.generation() == 430
+        b.close()
+    finally:
+        gol.gol_set_stream(None)
