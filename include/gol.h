@@ -197,11 +197,6 @@ const char *gol_last_error(void);
  *                          1 = it rotates them by renaming (fewer issued
  *                          instructions), -1 (default) = 1 for launches of
  *                          several boards, 0 for one; results are identical
- *   GOL_OPT_SCHEDULER      0 (default) = every warp owns a fixed set of units
- *                          for the whole launch (cooperative launch) and runs
- *                          each unit's passes as its neighbours allow;
- *                          1 = warps take (unit, pass) tasks from a shared
- *                          queue; results are identical
  * Unknown keys or values are GOL_EINVAL. */
 #define GOL_OPT_GENS_PER_PASS 1
 #define GOL_OPT_TILE_ROWS 2
@@ -210,7 +205,6 @@ const char *gol_last_error(void);
 #define GOL_OPT_ORIENTATION 5
 #define GOL_OPT_CHAIN_PERMILLE 6
 #define GOL_OPT_PIPELINE 7
-#define GOL_OPT_SCHEDULER 8
 int gol_set_option(int key, int64_t value);
 int gol_get_option(int key, int64_t *value);
 

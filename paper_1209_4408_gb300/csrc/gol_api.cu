@@ -8,7 +8,6 @@
 #include <map>
 #include <memory>
 #include <mutex>
-#include <queue>
 #include <string>
 #include <unordered_set>
 #include <vector>
@@ -80,7 +79,6 @@ void *g_alloc_ctx = nullptr;
 int64_t g_opt_k = 0, g_opt_rows = 0, g_opt_graphs = 1, g_opt_timeout_ms = 5000, g_opt_orient = 0;
 int64_t g_opt_chain = 0;     // chain cap, per mille of the average work per warp slot (0 = auto)
 int64_t g_opt_variant = -1;  // step kernel variant (see launch_persistent), -1 = auto
-int64_t g_opt_sched = 1;     // 0 static unit ownership, 1 dynamic work queue
 uint64_t g_serial = 0;
 
 struct DeviceState {
@@ -204,9 +202,8 @@ struct Plan {
     std::vector<uint64_t> serials;
     int K = 8;
     bool torus = true;
-    int64_t opt_k = 0, opt_rows = 0, opt_chain = 0, opt_variant = 0, opt_sched = 0;
+    int64_t opt_k = 0, opt_rows = 0, opt_chain = 0, opt_variant = 0;
     int variant = 0;
-    int sched = 0;   // 0 static ownership (cooperative launch), 1 dynamic queue
     // host copies
     std::vector<BoardDesc> boards;
     std::vector<UnitDesc> units;
@@ -260,11 +257,10 @@ cudaError_t occupancy_for(int K, bool torus, int v, int *bps) {
     }
     return cudaErrorInvalidValue;
 }
-cudaError_t launch_for(int K, const PersistArgs &a, bool torus, int variant, int grid, cudaStream_t s,
-                       bool cooperative = false) {
+cudaError_t launch_for(int K, const PersistArgs &a, bool torus, int variant, int grid, cudaStream_t s) {
     switch (K) {
 #define X(KV) \
-    case KV: return launch_persistent<KV>(a, torus, variant, grid, s, cooperative);
+    case KV: return launch_persistent<KV>(a, torus, variant, grid, s);
         GOL_FOR_EACH_K(X)
 #undef X
     }
@@ -405,7 +401,6 @@ int build_plan(Plan &P) {
     }
     P.K = supported_k(std::max(1, K));
     P.variant = plan_variant(n);
-    P.sched = (int)g_opt_sched;
     int bps = 1;
     cudaError_t e = occupancy_for(P.K, P.torus, P.variant, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -456,47 +451,14 @@ int build_plan(Plan &P) {
         return fail(GOL_EINVAL, "batch too large for one launch (%lld tasks)", (long long)P.total_tasks);
     const size_t nb = P.boards.size(), nu = P.units.size();
     const int64_t max_blocks = (int64_t)g_dev.sms * std::max(1, bps);
-    // Static ownership: units are dealt to warps longest-work-first onto the
-    // least loaded warp (work = passes x rows streamed per pass).
-    std::vector<int32_t> warp_units, warp_off;
-    int nwarps = 0;
-    if (P.sched == 0) {
-        nwarps = (int)std::min<int64_t>((int64_t)nu, max_blocks * kWarpsPerBlock);
-        std::vector<std::pair<double, int32_t>> w(nu);
-        for (size_t u = 0; u < nu; ++u) {
-            const UnitDesc &ud = P.units[u];
-            w[u] = {(double)P.boards[ud.board].npass * (ud.H + 2.0 * P.K), (int32_t)u};
-        }
-        std::stable_sort(w.begin(), w.end(), [](const std::pair<double, int32_t> &x,
-                                                 const std::pair<double, int32_t> &y) { return x.first > y.first; });
-        std::vector<std::vector<int32_t>> lists(nwarps);
-        std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>,
-                            std::greater<std::pair<double, int>>> heap;
-        for (int i = 0; i < nwarps; ++i) heap.push({0.0, i});
-        for (const auto &it : w) {
-            auto top = heap.top();
-            heap.pop();
-            lists[top.second].push_back(it.second);
-            heap.push({top.first + it.first, top.second});
-        }
-        warp_off.resize(nwarps + 1);
-        warp_units.reserve(nu);
-        for (int i = 0; i < nwarps; ++i) {
-            warp_off[i] = (int32_t)warp_units.size();
-            warp_units.insert(warp_units.end(), lists[i].begin(), lists[i].end());
-        }
-        warp_off[nwarps] = (int32_t)warp_units.size();
-    }
-    // device memory: boards | units | done | claimed | ctr | ring  (dynamic)
-    //                boards | units | done | ctr | warp_units | warp_off  (static)
+    // device memory: boards | units | done | claimed | ctr | ring
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t o_units = al(nb * sizeof(BoardDesc));
     const size_t o_done = o_units + al(nu * sizeof(UnitDesc));
     const size_t o_claimed = o_done + al(nu * 4);
-    const size_t o_ctr = o_claimed + (P.sched == 0 ? 0 : al(nu * 4));
+    const size_t o_ctr = o_claimed + al(nu * 4);
     const size_t o_ring = o_ctr + al((4 + nb) * 4);
-    const size_t o_woff = o_ring + al((P.sched == 0 ? nu : (size_t)P.total_tasks) * 4);
-    P.dbytes = o_woff + (P.sched == 0 ? al((size_t)(nwarps + 1) * 4) : 0);
+    P.dbytes = o_ring + al((size_t)P.total_tasks * 4);
     P.dmem = dev_alloc(P.dbytes, g_alloc, g_alloc_ctx);
     P.free_fn = g_free;
     P.alloc_ctx = g_alloc_ctx;
@@ -516,32 +478,15 @@ int build_plan(Plan &P) {
     a.nunits = (int32_t)nu;
     a.total_tasks = (int32_t)P.total_tasks;
     a.timeout_ns = g_opt_timeout_ms * 1000000ll;
-    a.warp_units = nullptr;
-    a.warp_off = nullptr;
-    a.nwarps = 0;
-    if (P.sched == 0) {
-        a.claimed = nullptr;
-        a.ring = nullptr;
-        CU(cudaMemcpyAsync(base + o_ring, warp_units.data(), nu * 4, cudaMemcpyHostToDevice, g_stream));
-        CU(cudaMemcpyAsync(base + o_woff, warp_off.data(), (nwarps + 1) * 4, cudaMemcpyHostToDevice, g_stream));
-        a.warp_units = (const int32_t *)(base + o_ring);
-        a.warp_off = (const int32_t *)(base + o_woff);
-        a.nwarps = nwarps;
-        P.grid = (int)std::max<int64_t>(1, ((int64_t)nwarps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-        // the host copies above are pageable: wait for them before the
-        // vectors go out of scope
-        CU(cudaStreamSynchronize(g_stream));
-    } else {
-        const int64_t want = (int64_t)(nu + kWarpsPerBlock - 1) / kWarpsPerBlock;
-        P.grid = (int)std::max<int64_t>(1, std::min(max_blocks, want));
-    }
+    const int64_t want = (int64_t)(nu + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    P.grid = (int)std::max<int64_t>(1, std::min(max_blocks, want));
     return GOL_OK;
 }
 
 cudaError_t launch_plan_kernels(const Plan &P, cudaStream_t s) {
     cudaError_t e = launch_sched_init(P.args, (int)P.boards.size(), s);
     if (e != cudaSuccess) return e;
-    return launch_for(P.K, P.args, P.torus, P.variant, P.grid, s, P.sched == 0);
+    return launch_for(P.K, P.args, P.torus, P.variant, P.grid, s);
 }
 
 // plan cache (most recently used first); evicted plans wait in the
@@ -592,7 +537,7 @@ Plan *find_plan(const std::vector<gol_handle> &hs, const std::vector<int64_t> &g
     for (size_t i = 0; i < g_plans.size(); ++i) {
         Plan &P = *g_plans[i];
         if (P.torus != torus || P.hs.size() != hs.size() || P.opt_k != g_opt_k || P.opt_rows != g_opt_rows ||
-            P.opt_chain != g_opt_chain || P.opt_variant != g_opt_variant || P.opt_sched != g_opt_sched)
+            P.opt_chain != g_opt_chain || P.opt_variant != g_opt_variant)
             continue;
         if (P.gens != gens || P.hs != hs) continue;
         bool same = true;
@@ -629,7 +574,6 @@ int run_packed(const std::vector<gol_handle> &hs, const std::vector<int64_t> &ge
         np->opt_rows = g_opt_rows;
         np->opt_chain = g_opt_chain;
         np->opt_variant = g_opt_variant;
-        np->opt_sched = g_opt_sched;
 
         for (auto h : hs) np->serials.push_back(h->serial);
         int rc = build_plan(*np);
@@ -1195,10 +1139,6 @@ int gol_set_option(int key, int64_t v) {
             if (v < -1 || v > 1) return fail(GOL_EINVAL, "pipeline variant must be -1, 0 or 1");
             g_opt_variant = v;
             return GOL_OK;
-        case GOL_OPT_SCHEDULER:
-            if (v < 0 || v > 1) return fail(GOL_EINVAL, "scheduler must be 0 or 1");
-            g_opt_sched = v;
-            return GOL_OK;
     }
     return fail(GOL_EINVAL, "unknown option %d", key);
 }
@@ -1213,7 +1153,6 @@ int gol_get_option(int key, int64_t *v) {
         case GOL_OPT_ORIENTATION: *v = g_opt_orient; return GOL_OK;
         case GOL_OPT_CHAIN_PERMILLE: *v = g_opt_chain; return GOL_OK;
         case GOL_OPT_PIPELINE: *v = g_opt_variant; return GOL_OK;
-        case GOL_OPT_SCHEDULER: *v = g_opt_sched; return GOL_OK;
     }
     return fail(GOL_EINVAL, "unknown option %d", key);
 }

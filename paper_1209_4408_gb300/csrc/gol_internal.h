@@ -76,14 +76,6 @@ struct PersistArgs {
     int32_t nunits;
     int32_t total_tasks;
     int64_t timeout_ns; // bounded waits give up after this long without progress
-    // Static ownership (when warp_off is not null): warp w owns the units
-    // warp_units[warp_off[w] .. warp_off[w+1]) for the whole launch and runs
-    // their passes whenever their neighbours allow; ring and claimed are
-    // unused.  The launch is cooperative, so all warps are resident.
-    const int32_t *warp_units;
-    const int32_t *warp_off;
-    int32_t nwarps;
-    int32_t pad;
 };
 
 // One board of a many-board transfer: `nwords` words of the board buffer
@@ -130,8 +122,7 @@ struct CopyDesc {
 // variant 0: window rows shift by register moves (fewer registers);
 // variant 1: window slots rotate by renaming (fewer issued instructions).
 template <int K>
-cudaError_t launch_persistent(const PersistArgs &a, bool torus, int variant, int grid, cudaStream_t s,
-                              bool cooperative = false);
+cudaError_t launch_persistent(const PersistArgs &a, bool torus, int variant, int grid, cudaStream_t s);
 template <int K>
 cudaError_t persistent_occupancy(bool torus, int variant, int *blocks_per_sm);
 

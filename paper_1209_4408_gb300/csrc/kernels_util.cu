@@ -18,14 +18,14 @@ int grid_for(int64_t n, int block = kBlock, int64_t cap = 1 << 20) {
 
 // --- scheduler state ------------------------------------------------------
 __global__ void sched_init_kernel(PersistArgs a, int nboards) {
-    const int64_t n = max(max((int64_t)a.nunits, a.ring ? (int64_t)a.total_tasks : 0), (int64_t)nboards);
+    const int64_t n = max(max((int64_t)a.nunits, (int64_t)a.total_tasks), (int64_t)nboards);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (i < a.nunits) {
             a.done[i] = 0;
-            if (a.claimed) a.claimed[i] = 1;   // every unit's first pass is queued below
+            a.claimed[i] = 1;   // every unit's first pass is queued below
         }
-        if (a.ring && i < a.total_tasks) a.ring[i] = i < a.nunits ? (int32_t)i : -1;
+        if (i < a.total_tasks) a.ring[i] = i < a.nunits ? (int32_t)i : -1;
         if (i < nboards) a.ctr[4 + i] = 0;
         if (i == 0) {
             a.ctr[0] = 0;         // next ticket
@@ -298,7 +298,7 @@ __global__ void int_probe_kernel(unsigned *sink, int iters) {
 }  // namespace
 
 cudaError_t launch_sched_init(const PersistArgs &a, int nboards, cudaStream_t s) {
-    const int64_t n = max(max((int64_t)a.nunits, a.ring ? (int64_t)a.total_tasks : 0), (int64_t)max(nboards, 1));
+    const int64_t n = max(max((int64_t)a.nunits, (int64_t)a.total_tasks), (int64_t)max(nboards, 1));
     sched_init_kernel<<<grid_for(n, kBlock, 4096), kBlock, 0, s>>>(a, nboards);
     return cudaGetLastError();
 }

@@ -561,128 +561,10 @@ __device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pa
 }
 
 template <int K, bool TORUS, int VARIANT>
-__device__ __forceinline__ void run_pass_of(const BoardDesc &bd, const UnitDesc &ud, int pass, int cur) {
-    const uint64_t *src = bd.buf[(cur + pass - 1) & 1];
-    uint64_t *dst = bd.buf[(cur + pass) & 1];
-    const int kk = pass_gens(bd, pass);
-    if (VARIANT == 0) {
-        if (kk == K)
-            run_unit_pass_moves<K, TORUS, false>(bd, ud, src, dst, K);
-        else
-            run_unit_pass_moves<K, TORUS, true>(bd, ud, src, dst, kk);
-    } else {
-        if (kk == K)
-            run_unit_pass<K, TORUS, false>(bd, ud, src, dst, K);
-        else
-            run_unit_pass<K, TORUS, true>(bd, ud, src, dst, kk);
-    }
-}
-
-// Lane 0: no owned unit is ready.  Sleeps a little; returns false (after
-// recording GOL_ETIMEOUT) when no task anywhere completed for timeout_ns or
-// another warp already gave up.
-static __device__ bool static_wait(const PersistArgs &A, uint64_t &t_last, int &seen, unsigned &ns) {
-    if (ld_acquire(&A.ctr[3]) != 0) return false;
-    const int c = ld_acquire(&A.ctr[2]);
-    const uint64_t now = global_ns();
-    if (c != seen) {
-        seen = c;
-        t_last = now;
-    } else if (now - t_last > (uint64_t)A.timeout_ns) {
-        atomicCAS(&A.ctr[3], 0, GOL_ETIMEOUT);
-        atomicCAS(A.sticky, 0, GOL_ETIMEOUT);
-        return false;
-    }
-    __nanosleep(ns);
-    if (ns < 2048) ns <<= 1;
-    return true;
-}
-
-// Static ownership: this warp runs the passes of its own units, each as soon
-// as the unit's neighbours have finished the previous pass.  Lanes examine up
-// to 32 owned units at once, starting from the one run last.  Deadlock-free:
-// the unit with the fewest completed passes always has its neighbours at or
-// beyond its pass, and its owner is resident (cooperative launch) and keeps
-// scanning.
-template <int K, bool TORUS, int VARIANT>
-__device__ void static_owner_loop(const PersistArgs &A) {
-    constexpr unsigned kFull = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    if (warp >= A.nwarps) return;
-    const int begin = A.warp_off[warp], n = A.warp_off[warp + 1] - begin;
-    int left = n, at = 0;
-    uint64_t t_last = global_ns();
-    int seen = -1;
-    unsigned ns = 64;
-    while (left > 0) {
-        int pick = -1, pass = 0;
-        for (int base = 0; base < n && pick < 0; base += 32) {
-            const int i = base + lane;
-            int u = -1, d = 0;
-            bool ready = false;
-            if (i < n) {
-                int c = at + i;
-                if (c >= n) c -= n;
-                u = A.warp_units[begin + c];
-                d = ld_relaxed(&A.done[u]);   // written only by this warp
-                const UnitDesc &ud = A.units[u];
-                if (d < A.boards[ud.board].npass) {
-                    int lo = d;
-#pragma unroll
-                    for (int k = 0; k < kMaxNeighbours; ++k)
-                        if (k < ud.nnb) lo = min(lo, ld_relaxed(&A.done[ud.nb[k]]));
-                    ready = lo >= d;
-                }
-            }
-            const unsigned m = __ballot_sync(kFull, ready);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                pick = __shfl_sync(kFull, u, leader);
-                pass = __shfl_sync(kFull, d, leader) + 1;
-                at += base + leader;
-                if (at >= n) at -= n;
-            }
-        }
-        if (pick < 0) {
-            bool go = true;
-            if (lane == 0) go = static_wait(A, t_last, seen, ns);
-            if (!__shfl_sync(kFull, (int)go, 0)) return;
-            continue;
-        }
-        ns = 64;
-        // the neighbours' counters were read relaxed: order their pass data
-        // before this pass's loads
-        fence_acq_rel_gpu();
-        const UnitDesc &ud = A.units[pick];
-        const BoardDesc &bd = A.boards[ud.board];
-        int cur = 0;
-        if (lane == 0) cur = ld_acquire(bd.cur);
-        cur = __shfl_sync(kFull, cur, 0);
-        run_pass_of<K, TORUS, VARIANT>(bd, ud, pass, cur);
-        fence_acq_rel_gpu();
-        __syncwarp();
-        if (lane == 0) {
-            st_release(&A.done[pick], pass);
-            red_add(&A.ctr[2], 1);
-            if (pass == bd.npass && atomicAdd(&A.ctr[4 + ud.board], 1) == bd.nunits - 1) {
-                if (bd.npass & 1) *bd.cur ^= 1;
-                A.ctr[4 + ud.board] = 0;
-            }
-        }
-        if (pass == bd.npass) --left;
-    }
-}
-
-template <int K, bool TORUS, int VARIANT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 persistent_step_kernel(const PersistArgs A) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    if (A.warp_off) {
-        static_owner_loop<K, TORUS, VARIANT>(A);
-        return;
-    }
     int u = -1;
     for (;;) {
         if (u < 0) {
@@ -728,16 +610,18 @@ persistent_step_kernel(const PersistArgs A) {
 }
 
 template <int K>
-cudaError_t launch_persistent_impl(const PersistArgs &a, bool torus, int variant, int grid, cudaStream_t s,
-                                   bool cooperative) {
-    void (*fn)(PersistArgs) = variant == 0 ? (torus ? persistent_step_kernel<K, true, 0> : persistent_step_kernel<K, false, 0>)
-                                           : (torus ? persistent_step_kernel<K, true, 1> : persistent_step_kernel<K, false, 1>);
-    if (cooperative) {
-        PersistArgs copy = a;
-        void *args[] = {&copy};
-        return cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(kWarpsPerBlock * 32), args, 0, s);
+cudaError_t launch_persistent_impl(const PersistArgs &a, bool torus, int variant, int grid, cudaStream_t s) {
+    if (variant == 0) {
+        if (torus)
+            persistent_step_kernel<K, true, 0><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+        else
+            persistent_step_kernel<K, false, 0><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+    } else {
+        if (torus)
+            persistent_step_kernel<K, true, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+        else
+            persistent_step_kernel<K, false, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
     }
-    fn<<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -754,8 +638,8 @@ cudaError_t persistent_occupancy_impl(bool torus, int variant, int *bps) {
 #define GOL_INSTANTIATE_PERSISTENT(KV)                                                             \
     template <>                                                                                    \
     cudaError_t launch_persistent<KV>(const PersistArgs &a, bool torus, int variant, int grid,     \
-                                      cudaStream_t s, bool cooperative) {                          \
-        return launch_persistent_impl<KV>(a, torus, variant, grid, s, cooperative);                \
+                                      cudaStream_t s) {                                            \
+        return launch_persistent_impl<KV>(a, torus, variant, grid, s);                             \
     }                                                                                              \
     template <>                                                                                    \
     cudaError_t persistent_occupancy<KV>(bool torus, int variant, int *bps) {                      \

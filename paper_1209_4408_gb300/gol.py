@@ -40,7 +40,6 @@ GOL_OPT_WAIT_TIMEOUT_MS = 4
 GOL_OPT_ORIENTATION = 5
 GOL_OPT_CHAIN_PERMILLE = 6
 GOL_OPT_PIPELINE = 7
-GOL_OPT_SCHEDULER = 8
 
 # every symbol declared in include/gol.h
 EXPORTED = (
