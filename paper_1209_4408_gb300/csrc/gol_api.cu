@@ -456,7 +456,7 @@ int build_plan(Plan &P) {
     const size_t o_units = al(nb * sizeof(BoardDesc));
     const size_t o_done = o_units + al(nu * sizeof(UnitDesc));
     const size_t o_claimed = o_done + al(nu * 4);
-    const size_t o_ctr = o_claimed + al(nu * 4);
+    const size_t o_ctr = o_claimed + al(2 * nu * 4);
     const size_t o_ring = o_ctr + al((4 + nb) * 4);
     P.dbytes = o_ring + al((size_t)P.total_tasks * 4);
     P.dmem = dev_alloc(P.dbytes, g_alloc, g_alloc_ctx);
@@ -1265,7 +1265,7 @@ constexpr int kStaticMaxTasks = 1 << 18;       // queue slots per launch
 constexpr size_t kSaUnits = 256;               // offsets in the static workspace
 constexpr size_t kSaDone = kSaUnits + sizeof(UnitDesc) * kStaticMaxUnits;
 constexpr size_t kSaClaimed = kSaDone + 4 * (size_t)kStaticMaxUnits;
-constexpr size_t kSaCtr = kSaClaimed + 4 * (size_t)kStaticMaxUnits;
+constexpr size_t kSaCtr = kSaClaimed + 8 * (size_t)kStaticMaxUnits;
 constexpr size_t kSaStatus = kSaCtr + 256;     // [0] status, [1] current buffer
 constexpr size_t kSaRing = kSaStatus + 256;
 constexpr size_t kStaticBytes = kSaRing + 4 * (size_t)kStaticMaxTasks;   // about 1.3 MiB

@@ -33,14 +33,11 @@
 // output its halo touches (its neighbours) and overwrites the buffer those
 // units read during pass p-1; it may start once all of them have completed
 // pass p-1.  Warps take work from a global queue (tickets on head, slots
-// filled in order); after a pass a warp publishes done[u] = p, issues a
-// sequentially consistent fence and re-examines u and its neighbours: a unit
-// whose neighbours have all caught up is claimed with a CAS on claimed[] and
-// either run next by the same warp or appended to the queue.  The fence
-// makes the last of several concurrent completers see all their stores, so
-// no ready unit is missed.  Every wait is bounded: a waiter gives up after
-// `timeout_ns` without any task completing, records GOL_ETIMEOUT and
-// returns.
+// filled in order); after a pass a warp adds one to the join counter of u and
+// of each neighbour (complete_pass): the finisher that completes a counter
+// claims that unit and either runs it next in the same warp or appends it to
+// the queue.  Every wait is bounded: a waiter gives up after `timeout_ns`
+// without any task completing, records GOL_ETIMEOUT and returns.
 #pragma once
 
 #include <type_traits>
@@ -88,7 +85,6 @@ __device__ __forceinline__ int ld_acquire(const int32_t *p) {
 __device__ __forceinline__ void st_release(int32_t *p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ void fence_sc_gpu() { asm volatile("fence.sc.gpu;" ::: "memory"); }
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -502,17 +498,31 @@ __device__ __forceinline__ void red_add(int32_t *p, int v) {
     asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Whole warp, after unit u finished pass `pass`: publish it and schedule the
-// units it may have made ready.  Lane i examines candidate i (u itself, then
-// its neighbours), so the loads of all candidates overlap.  Returns the unit
-// this warp runs next (u first if it is ready) or -1.
+__device__ __forceinline__ int atom_add_acq_rel(int32_t *p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Whole warp, after unit u finished pass `pass`, with every lane's stores of
+// the pass already ordered by an acquire-release fence and a warp barrier.
+//
+// Join counters: unit v may run pass q+1 once v and each of its nnb(v)
+// neighbours have finished pass q.  Every finisher of pass q adds one to
+// join[v][q & 1] for itself and each of its neighbours (the relation is
+// symmetric); the add that brings the counter to nnb(v) + 1 makes v ready,
+// and only that one thread sees it, so v is claimed exactly once.  The
+// claimer resets the counter before v can run again, and a neighbour is
+// never more than one pass ahead of v, so two parities suffice.  Lane i
+// handles candidate i (u itself, then its neighbours); the first ready lane
+// continues in this warp, the others go to the queue.  Returns the unit
+// this warp runs next or -1.
 __device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pass, const UnitDesc &ud,
                                              const BoardDesc &bd) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int npass = bd.npass;
     if (lane == 0) {
-        st_release(&A.done[u], pass);
         red_add(&A.ctr[2], 1);
         if (pass == npass) {
             // last unit of the board to finish flips the board's current buffer
@@ -522,36 +532,19 @@ __device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pa
             }
         }
     }
-    __syncwarp();
-    if (ud.nnb == 0) {
-        // a unit with no neighbours (a board of one unit) depends on nobody
-        // but itself: run its next pass at once, without fences or a claim
-        if (pass >= npass) return -1;
-        if (lane == 0) A.claimed[u] = pass + 1;
-        return u;
-    }
-    // Every completer orders its `done` store before its reads of the other
-    // counters with a sequentially consistent fence: of two units finishing at
-    // the same time, at least one sees the other's store.
-    fence_sc_gpu();
-    int v = -1, d = 0;
+    if (pass >= npass) return -1;            // no unit of this board runs again
+    if (ud.nnb == 0) return u;               // a board of one unit waits for nobody
+    int v = -1;
     bool ready = false;
     if (lane <= ud.nnb) {
         v = lane == 0 ? u : A.units[u].nb[lane - 1];
-        d = ld_relaxed(&A.done[v]);
-        const int cl = ld_relaxed(&A.claimed[v]);
-        if (d < npass && cl == d) {
-            const UnitDesc &vd = A.units[v];
-            const int m = vd.nnb;
-            int lo = d;
-#pragma unroll
-            for (int k = 0; k < kMaxNeighbours; ++k)
-                if (k < m) lo = min(lo, ld_relaxed(&A.done[vd.nb[k]]));
-            ready = lo >= d;
+        int32_t *j = &A.claimed[2 * v + (pass & 1)];
+        if (atom_add_acq_rel(j, 1) == A.units[v].nnb) {
+            *j = 0;
+            A.done[v] = pass + 1;            // the pass v runs next
+            ready = true;
         }
     }
-    fence_acq_rel_gpu();
-    if (ready) ready = atomicCAS(&A.claimed[v], d, d + 1) == d;
     const unsigned mask = __ballot_sync(kFull, ready);
     if (!mask) return -1;
     const int leader = __ffs(mask) - 1;
@@ -582,7 +575,7 @@ persistent_step_kernel(const PersistArgs A) {
         const BoardDesc bd = A.boards[ud.board];
         int pass = 0, cur = 0;
         if (lane == 0) {
-            pass = ld_acquire(&A.done[u]) + 1;
+            pass = ld_acquire(&A.done[u]);   // written by the thread that made u ready
             cur = ld_acquire(bd.cur);
         }
         pass = __shfl_sync(kFull, pass, 0);
@@ -601,11 +594,13 @@ persistent_step_kernel(const PersistArgs A) {
             else
                 run_unit_pass<K, TORUS, true>(bd, ud, src, dst, kk);
         }
-        // every lane's stores of this pass are ordered before lane 0's
-        // release of done[u] (acquire-release fence, then the warp barrier)
+        // every lane's stores of this pass are ordered before the counter
+        // updates that publish it (acquire-release fence, then the warp barrier)
         fence_acq_rel_gpu();
         __syncwarp();
-        u = complete_pass(A, u, pass, ud, bd);
+        const int next = complete_pass(A, u, pass, ud, bd);
+        if (next == u && ud.nnb == 0 && lane == 0) A.done[u] = pass + 1;
+        u = next;
     }
 }
 
