@@ -558,7 +558,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 persistent_step_kernel(const PersistArgs A) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    int u = -1;
+    int u = -1, pass = 0, cur = 0;
+    bool same = false;   // continuing with the unit just run: pass and buffer known
     for (;;) {
         if (u < 0) {
             int t = 0;
@@ -570,16 +571,20 @@ persistent_step_kernel(const PersistArgs A) {
             v = __shfl_sync(kFull, v, 0);
             if (v < 0) return;
             u = v;
+            same = false;
         }
         const UnitDesc ud = A.units[u];
         const BoardDesc bd = A.boards[ud.board];
-        int pass = 0, cur = 0;
-        if (lane == 0) {
-            pass = ld_acquire(&A.done[u]);   // written by the thread that made u ready
-            cur = ld_acquire(bd.cur);
+        if (same) {
+            ++pass;          // a board's buffer index only changes after its last pass
+        } else {
+            if (lane == 0) {
+                pass = ld_acquire(&A.done[u]);   // written by the thread that made u ready
+                cur = ld_acquire(bd.cur);
+            }
+            pass = __shfl_sync(kFull, pass, 0);
+            cur = __shfl_sync(kFull, cur, 0);
         }
-        pass = __shfl_sync(kFull, pass, 0);
-        cur = __shfl_sync(kFull, cur, 0);
         const uint64_t *src = bd.buf[(cur + pass - 1) & 1];
         uint64_t *dst = bd.buf[(cur + pass) & 1];
         const int kk = pass_gens(bd, pass);
@@ -599,7 +604,7 @@ persistent_step_kernel(const PersistArgs A) {
         fence_acq_rel_gpu();
         __syncwarp();
         const int next = complete_pass(A, u, pass, ud, bd);
-        if (next == u && ud.nnb == 0 && lane == 0) A.done[u] = pass + 1;
+        same = next == u;
         u = next;
     }
 }
