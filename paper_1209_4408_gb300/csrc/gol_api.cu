@@ -78,7 +78,7 @@ void (*g_free)(void *, void *) = nullptr;
 void *g_alloc_ctx = nullptr;
 int64_t g_opt_k = 0, g_opt_rows = 0, g_opt_graphs = 1, g_opt_timeout_ms = 5000, g_opt_orient = 0;
 int64_t g_opt_chain = 0;     // chain cap, per mille of the average work per warp slot (0 = auto)
-int64_t g_opt_variant = -1;  // step kernel variant (see launch_persistent), -1 = auto
+int64_t g_opt_variant = -1;  // step kernel variant (see launch_persistent), -1 = default
 uint64_t g_serial = 0;
 
 struct DeviceState {
@@ -241,12 +241,10 @@ int supported_k(int k) {
         if (v <= k) s = v;
     return s;
 }
-// Kernel variant of a plan: renaming rotation (1) measured faster on the
-// 4096-board batch, register moves (0) on a single 16384^2 board.
-int plan_variant(size_t nboards) {
-    if (g_opt_variant >= 0) return (int)g_opt_variant;
-    return nboards > 1 ? 1 : 0;
-}
+// Kernel variant of a plan: the window rotation by renaming (1) measured
+// faster than register moves (0) on both the 4096-board batch and a 16384^2
+// board once the join-counter scheduler removed most per-pass overhead.
+int plan_variant(size_t) { return g_opt_variant >= 0 ? (int)g_opt_variant : 1; }
 
 cudaError_t occupancy_for(int K, bool torus, int v, int *bps) {
     switch (K) {
@@ -451,12 +449,12 @@ int build_plan(Plan &P) {
         return fail(GOL_EINVAL, "batch too large for one launch (%lld tasks)", (long long)P.total_tasks);
     const size_t nb = P.boards.size(), nu = P.units.size();
     const int64_t max_blocks = (int64_t)g_dev.sms * std::max(1, bps);
-    // device memory: boards | units | done | claimed | ctr | ring
+    // device memory: boards | units | next_pass | join | ctr | ring
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t o_units = al(nb * sizeof(BoardDesc));
-    const size_t o_done = o_units + al(nu * sizeof(UnitDesc));
-    const size_t o_claimed = o_done + al(nu * 4);
-    const size_t o_ctr = o_claimed + al(2 * nu * 4);
+    const size_t o_next = o_units + al(nu * sizeof(UnitDesc));
+    const size_t o_join = o_next + al(nu * 4);
+    const size_t o_ctr = o_join + al(2 * nu * 4);
     const size_t o_ring = o_ctr + al((4 + nb) * 4);
     P.dbytes = o_ring + al((size_t)P.total_tasks * 4);
     P.dmem = dev_alloc(P.dbytes, g_alloc, g_alloc_ctx);
@@ -470,8 +468,8 @@ int build_plan(Plan &P) {
     PersistArgs &a = P.args;
     a.boards = (const BoardDesc *)base;
     a.units = (const UnitDesc *)(base + o_units);
-    a.done = (int32_t *)(base + o_done);
-    a.claimed = (int32_t *)(base + o_claimed);
+    a.next_pass = (int32_t *)(base + o_next);
+    a.join = (int32_t *)(base + o_join);
     a.ctr = (int32_t *)(base + o_ctr);
     a.ring = (int32_t *)(base + o_ring);
     a.sticky = g_dev.sticky;
@@ -1229,8 +1227,8 @@ int gol_debug_unfilled_wait(int64_t timeout_ms) {
     char *base = (char *)ws.p;
     a.boards = nullptr;
     a.units = nullptr;
-    a.done = (int32_t *)(base + 0);
-    a.claimed = (int32_t *)(base + 256);
+    a.next_pass = (int32_t *)(base + 0);
+    a.join = (int32_t *)(base + 256);
     a.ctr = (int32_t *)(base + 512);
     a.ring = (int32_t *)(base + 1024);
     a.sticky = g_dev.sticky;
@@ -1263,9 +1261,9 @@ namespace {
 constexpr int kStaticMaxUnits = 4096;          // units of one board
 constexpr int kStaticMaxTasks = 1 << 18;       // queue slots per launch
 constexpr size_t kSaUnits = 256;               // offsets in the static workspace
-constexpr size_t kSaDone = kSaUnits + sizeof(UnitDesc) * kStaticMaxUnits;
-constexpr size_t kSaClaimed = kSaDone + 4 * (size_t)kStaticMaxUnits;
-constexpr size_t kSaCtr = kSaClaimed + 8 * (size_t)kStaticMaxUnits;
+constexpr size_t kSaNext = kSaUnits + sizeof(UnitDesc) * kStaticMaxUnits;
+constexpr size_t kSaJoin = kSaNext + 4 * (size_t)kStaticMaxUnits;
+constexpr size_t kSaCtr = kSaJoin + 8 * (size_t)kStaticMaxUnits;
 constexpr size_t kSaStatus = kSaCtr + 256;     // [0] status, [1] current buffer
 constexpr size_t kSaRing = kSaStatus + 256;
 constexpr size_t kStaticBytes = kSaRing + 4 * (size_t)kStaticMaxTasks;   // about 1.3 MiB
@@ -1333,8 +1331,8 @@ extern "C" int gol_step_packed_noalloc(uint64_t *d_board, uint64_t *d_spare, int
     PersistArgs a{};
     a.boards = (const BoardDesc *)base;
     a.units = (const UnitDesc *)(base + kSaUnits);
-    a.done = (int32_t *)(base + kSaDone);
-    a.claimed = (int32_t *)(base + kSaClaimed);
+    a.next_pass = (int32_t *)(base + kSaNext);
+    a.join = (int32_t *)(base + kSaJoin);
     a.ctr = (int32_t *)(base + kSaCtr);
     a.ring = (int32_t *)(base + kSaRing);
     a.sticky = (int32_t *)(base + kSaStatus);

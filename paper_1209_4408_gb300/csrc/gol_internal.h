@@ -67,8 +67,8 @@ struct UnitDesc {
 struct PersistArgs {
     const BoardDesc *boards;
     const UnitDesc *units;
-    int32_t *done;      // [nunits] the pass each unit runs next (set when it is claimed)
-    int32_t *claimed;   // [2 * nunits] join counters, one per pass parity
+    int32_t *next_pass; // [nunits] the pass each unit runs next (set when it is claimed)
+    int32_t *join;      // [2 * nunits] join counters, one per pass parity
     int32_t *ring;      // [total_tasks] work queue, -1 = empty slot
     int32_t *ctr;       // [0] head ticket, [1] tail slot, [2] tasks completed, [3] status,
                         // [4 + b] units of board b that finished all passes

@@ -22,9 +22,9 @@ __global__ void sched_init_kernel(PersistArgs a, int nboards) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (i < a.nunits) {
-            a.done[i] = 1;            // every unit's first pass is queued below
-            a.claimed[2 * i] = 0;     // join counters of both pass parities
-            a.claimed[2 * i + 1] = 0;
+            a.next_pass[i] = 1;            // every unit's first pass is queued below
+            a.join[2 * i] = 0;     // join counters of both pass parities
+            a.join[2 * i + 1] = 0;
         }
         if (i < a.total_tasks) a.ring[i] = i < a.nunits ? (int32_t)i : -1;
         if (i < nboards) a.ctr[4 + i] = 0;

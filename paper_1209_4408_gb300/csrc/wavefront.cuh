@@ -538,10 +538,10 @@ __device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pa
     bool ready = false;
     if (lane <= ud.nnb) {
         v = lane == 0 ? u : A.units[u].nb[lane - 1];
-        int32_t *j = &A.claimed[2 * v + (pass & 1)];
+        int32_t *j = &A.join[2 * v + (pass & 1)];
         if (atom_add_acq_rel(j, 1) == A.units[v].nnb) {
             *j = 0;
-            A.done[v] = pass + 1;            // the pass v runs next
+            A.next_pass[v] = pass + 1;            // the pass v runs next
             ready = true;
         }
     }
@@ -579,7 +579,7 @@ persistent_step_kernel(const PersistArgs A) {
             ++pass;          // a board's buffer index only changes after its last pass
         } else {
             if (lane == 0) {
-                pass = ld_acquire(&A.done[u]);   // written by the thread that made u ready
+                pass = ld_acquire(&A.next_pass[u]);   // written by the thread that made u ready
                 cur = ld_acquire(bd.cur);
             }
             pass = __shfl_sync(kFull, pass, 0);
