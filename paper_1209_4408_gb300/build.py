@@ -41,8 +41,21 @@ def _deps():
         [os.path.join(INCLUDE, "gol.h"), os.path.abspath(__file__)]
 
 
+STAMP = os.path.join(OUT_DIR, "flags.txt")
+
+
+def _extra_flags():
+    """Extra nvcc flags from GOL_NVCC_EXTRA (e.g. -DGOL_MIN_BLOCKS=8)."""
+    return os.environ.get("GOL_NVCC_EXTRA", "").split()
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
+        return False
+    try:
+        if open(STAMP).read() != " ".join(_extra_flags()):
+            return False
+    except OSError:
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(d) <= t for d in _deps())
@@ -53,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     exe = nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + _extra_flags()
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
@@ -76,6 +89,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(_extra_flags()))
     return LIB
 
 

@@ -553,8 +553,14 @@ __device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pa
     return next;
 }
 
+// Blocks per SM the register allocation must allow (GOL_MIN_BLOCKS at build
+// time; 1 leaves the choice to the compiler).
+#ifndef GOL_MIN_BLOCKS
+#define GOL_MIN_BLOCKS 1
+#endif
+
 template <int K, bool TORUS, int VARIANT>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, (K >= 4 && K <= 6) ? GOL_MIN_BLOCKS : 1)
 persistent_step_kernel(const PersistArgs A) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
