@@ -344,14 +344,24 @@ def run_gpu(args, rank, world, local):
         barrier()
         t0 = time.perf_counter()
         h2d = d2h = 0
+        phase = {"upload_s": 0.0, "step_s": 0.0, "download_s": 0.0}
         for _ in range(e2e_steps):
             if layout == gol.GOL_LAYOUT_PACKED:
                 # one upload of all boards, the step, one download of all boards
+                ta = time.perf_counter()
                 gol.gol_set_packed_batch(handles, host)
+                torch.cuda.synchronize()
+                tb = time.perf_counter()
                 h2d += host.nbytes
                 step()
+                torch.cuda.synchronize()
+                tc = time.perf_counter()
                 gol.gol_get_packed_batch(handles, host_out)
                 d2h += host_out.nbytes
+                td = time.perf_counter()
+                phase["upload_s"] += tb - ta
+                phase["step_s"] += tc - tb
+                phase["download_s"] += td - tc
             else:
                 cells = [synth.bernoulli_board(s.rows, s.cols, s.density, s.seed) for s in specs]
                 for b, c in zip(boards, cells):
@@ -363,7 +373,8 @@ def run_gpu(args, rank, world, local):
         barrier()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         e2e = {"value": total_cells_gens * world / e2e_s / 1e9, "unit": "GCUPS",
-               "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps}
+               "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
+               "ms_per_phase": {k: round(v / e2e_steps * 1e3, 3) for k, v in phase.items()}}
 
     # ---- roofline of the dominant kernel (the persistent step kernel) ---------------
     ops = float("nan") if args.no_probe else gol.gol_probe_int_throughput()[0]
