@@ -195,8 +195,10 @@ const char *gol_last_error(void);
  *   GOL_OPT_PIPELINE       0 = the step kernel shifts its three-row windows
  *                          by register moves (fewer registers, more warps),
  *                          1 = it rotates them by renaming (fewer issued
- *                          instructions), -1 (default) = 1; results are
- *                          identical
+ *                          instructions), 2 = renaming with skewed stages
+ *                          (stage g works one row behind stage g - 1, so the
+ *                          stages of a row step are independent), -1
+ *                          (default) = 1; results are identical
  * Unknown keys or values are GOL_EINVAL. */
 #define GOL_OPT_GENS_PER_PASS 1
 #define GOL_OPT_TILE_ROWS 2

@@ -903,11 +903,13 @@ int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords) {
 
 namespace {
 // shared checks of the many-board transfers; fills descriptors and offsets
-int many_plan(const gol_handle *hs, size_t n, size_t nwords, std::vector<CopyDesc> &d, bool scatter) {
+int many_plan(const gol_handle *hs, size_t n, size_t nwords, std::vector<CopyDesc> &d, bool scatter,
+              int64_t &blocks) {
     if (!hs) return fail(GOL_EINVAL, "null handle array");
     if (n > (size_t)(1 << 30)) return fail(GOL_EINVAL, "too many boards");
     std::unordered_set<gol_handle> seen;
     int64_t off = 0;
+    blocks = 0;
     d.resize(n);
     for (size_t i = 0; i < n; ++i) {
         gol_handle h = hs[i];
@@ -922,8 +924,12 @@ int many_plan(const gol_handle *hs, size_t n, size_t nwords, std::vector<CopyDes
         d[i].rows = h->rows;
         d[i].words = h->words;
         d[i].transposed = h->transposed;
+        d[i].pad = 0;
+        d[i].block0 = blocks;
+        blocks += copy_blocks(d[i]);
         off += nw;
     }
+    if (blocks > INT32_MAX) return fail(GOL_EINVAL, "too many words in one transfer");
     if ((size_t)off != nwords) return fail(GOL_EINVAL, "nwords = %zu, the boards hold %lld words", nwords, (long long)off);
     return GOL_OK;
 }
@@ -934,7 +940,8 @@ int gol_set_packed_batch(const gol_handle *hs, size_t n, const uint64_t *words, 
     if (n == 0) return GOL_OK;
     if (!words) return fail(GOL_EINVAL, "null words");
     std::vector<CopyDesc> d;
-    int rc = many_plan(hs, n, nwords, d, true);
+    int64_t blocks = 0;
+    int rc = many_plan(hs, n, nwords, d, true, blocks);
     if (rc) return rc;
     const size_t dbytes = (n * sizeof(CopyDesc) + 255) & ~size_t(255);
     Scratch st(dbytes + nwords * 8);
@@ -942,7 +949,7 @@ int gol_set_packed_batch(const gol_handle *hs, size_t n, const uint64_t *words, 
     CU(cudaMemcpyAsync(st.p, d.data(), n * sizeof(CopyDesc), cudaMemcpyHostToDevice, g_stream));
     uint64_t *stage = (uint64_t *)((char *)st.p + dbytes);
     CU(cudaMemcpyAsync(stage, words, nwords * 8, cudaMemcpyHostToDevice, g_stream));
-    CU(launch_scatter_boards((const CopyDesc *)st.p, (int)n, stage, g_stream));
+    CU(launch_scatter_boards((const CopyDesc *)st.p, (int)n, blocks, stage, g_stream));
     for (size_t i = 0; i < n; ++i) {
         hs[i]->cur = 0;
         hs[i]->generation = 0;
@@ -955,14 +962,15 @@ int gol_get_packed_batch(const gol_handle *hs, size_t n, uint64_t *words, size_t
     if (n == 0) return GOL_OK;
     if (!words) return fail(GOL_EINVAL, "null words");
     std::vector<CopyDesc> d;
-    int rc = many_plan(hs, n, nwords, d, false);
+    int64_t blocks = 0;
+    int rc = many_plan(hs, n, nwords, d, false, blocks);
     if (rc) return rc;
     const size_t dbytes = (n * sizeof(CopyDesc) + 255) & ~size_t(255);
     Scratch st(dbytes + nwords * 8);
     if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", nwords * 8);
     CU(cudaMemcpyAsync(st.p, d.data(), n * sizeof(CopyDesc), cudaMemcpyHostToDevice, g_stream));
     uint64_t *stage = (uint64_t *)((char *)st.p + dbytes);
-    CU(launch_gather_boards((const CopyDesc *)st.p, (int)n, stage, g_stream));
+    CU(launch_gather_boards((const CopyDesc *)st.p, (int)n, blocks, stage, g_stream));
     CU(cudaMemcpyAsync(words, stage, nwords * 8, cudaMemcpyDeviceToHost, g_stream));
     return sync_stream();
 }
@@ -1134,7 +1142,7 @@ int gol_set_option(int key, int64_t v) {
             g_opt_chain = v;
             return GOL_OK;
         case GOL_OPT_PIPELINE:
-            if (v < -1 || v > 1) return fail(GOL_EINVAL, "pipeline variant must be -1, 0 or 1");
+            if (v < -1 || v > 2) return fail(GOL_EINVAL, "pipeline variant must be -1, 0, 1 or 2");
             g_opt_variant = v;
             return GOL_OK;
     }

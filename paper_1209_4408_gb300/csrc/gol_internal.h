@@ -116,7 +116,19 @@ struct CopyDesc {
     int64_t words;
     int32_t transposed; // board stored transposed (see gol_api.cu)
     int32_t pad;
+    int64_t block0;     // first block of this board in the copy grid
 };
+
+// Copy grid: a board takes ceil(words / kCopyWordsPerBlock) blocks, or
+// ceil(tiles / kCopyTilesPerBlock) when stored transposed (64 x 64 cell
+// tiles), at least one; the boards' blocks are consecutive.
+constexpr int64_t kCopyWordsPerBlock = 4096;
+constexpr int64_t kCopyTilesPerBlock = 16;
+__host__ __device__ __forceinline__ int64_t copy_blocks(const CopyDesc &c) {
+    const int64_t n = c.transposed ? (c.rows / 64) * c.words : c.nwords;
+    const int64_t per = c.transposed ? kCopyTilesPerBlock : kCopyWordsPerBlock;
+    return n > 0 ? (n + per - 1) / per : 1;
+}
 
 // Launchers (one translation unit per K).  Return cudaGetLastError().
 // variant 0: window rows shift by register moves (fewer registers);
@@ -148,8 +160,8 @@ cudaError_t launch_popcount_packed(const uint64_t *words, int64_t n, unsigned lo
 cudaError_t launch_popcount_bytes(const uint8_t *cells, int64_t n, unsigned long long *out,
                                   cudaStream_t s);
 cudaError_t launch_convert(const uint64_t *src, uint64_t *dst, int64_t n, bool to_res, cudaStream_t s);
-cudaError_t launch_scatter_boards(const CopyDesc *d, int n, const uint64_t *staging, cudaStream_t s);
-cudaError_t launch_gather_boards(const CopyDesc *d, int n, uint64_t *staging, cudaStream_t s);
+cudaError_t launch_scatter_boards(const CopyDesc *d, int n, int64_t blocks, const uint64_t *staging, cudaStream_t s);
+cudaError_t launch_gather_boards(const CopyDesc *d, int n, int64_t blocks, uint64_t *staging, cudaStream_t s);
 cudaError_t launch_int_probe(unsigned *sink, int iters, int grid, int block, cudaStream_t s);
 int int_probe_ops_per_iter();   // 32-bit integer operations per thread per probe iteration
 

@@ -241,26 +241,45 @@ __global__ void orient_kernel(const uint64_t *__restrict__ src, uint64_t *__rest
 }
 
 // --- many boards <-> one contiguous staging buffer ----------------------------
-// block b copies the words of board b; a null `cur` is not written
-__global__ void scatter_boards_kernel(const CopyDesc *__restrict__ d, const uint64_t *__restrict__ staging) {
-    const CopyDesc c = d[blockIdx.x];
-    if (!c.transposed) {
-        for (int64_t i = threadIdx.x; i < c.nwords; i += blockDim.x) c.board[i] = to_resident(staging[c.offset + i]);
-    } else {
-        const int64_t tiles = (c.rows / 64) * c.words;
-        for (int64_t t = threadIdx.x / 32; t < tiles; t += blockDim.x / 32)
-            transpose_tile(staging + c.offset, c.words, t / c.words, t % c.words, c.board, c.rows / 64, false, true);
+// The copy grid holds copy_blocks(d[i]) consecutive blocks per board; a block
+// finds its board by binary search on block0 and copies its share of the
+// board's words (or 64 x 64 tiles when the board is stored transposed).
+__device__ __forceinline__ int copy_board_of_block(const CopyDesc *__restrict__ d, int n, int64_t b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].block0 <= b) lo = mid; else hi = mid - 1;
     }
-    if (threadIdx.x == 0 && c.cur) *c.cur = 0;
+    return lo;
 }
 
-__global__ void gather_boards_kernel(const CopyDesc *__restrict__ d, uint64_t *__restrict__ staging) {
-    const CopyDesc c = d[blockIdx.x];
+// a null `cur` is not written
+__global__ void scatter_boards_kernel(const CopyDesc *__restrict__ d, int n, const uint64_t *__restrict__ staging) {
+    const CopyDesc c = d[copy_board_of_block(d, n, blockIdx.x)];
+    const int64_t lb = blockIdx.x - c.block0;
     if (!c.transposed) {
-        for (int64_t i = threadIdx.x; i < c.nwords; i += blockDim.x) staging[c.offset + i] = to_interchange(c.board[i]);
+        const int64_t end = min(c.nwords, (lb + 1) * kCopyWordsPerBlock);
+        for (int64_t i = lb * kCopyWordsPerBlock + threadIdx.x; i < end; i += blockDim.x)
+            c.board[i] = to_resident(staging[c.offset + i]);
     } else {
-        const int64_t rb = c.rows / 64, tiles = rb * c.words;
-        for (int64_t t = threadIdx.x / 32; t < tiles; t += blockDim.x / 32)
+        const int64_t end = min((c.rows / 64) * c.words, (lb + 1) * kCopyTilesPerBlock);
+        for (int64_t t = lb * kCopyTilesPerBlock + threadIdx.x / 32; t < end; t += blockDim.x / 32)
+            transpose_tile(staging + c.offset, c.words, t / c.words, t % c.words, c.board, c.rows / 64, false, true);
+    }
+    if (lb == 0 && threadIdx.x == 0 && c.cur) *c.cur = 0;
+}
+
+__global__ void gather_boards_kernel(const CopyDesc *__restrict__ d, int n, uint64_t *__restrict__ staging) {
+    const CopyDesc c = d[copy_board_of_block(d, n, blockIdx.x)];
+    const int64_t lb = blockIdx.x - c.block0;
+    if (!c.transposed) {
+        const int64_t end = min(c.nwords, (lb + 1) * kCopyWordsPerBlock);
+        for (int64_t i = lb * kCopyWordsPerBlock + threadIdx.x; i < end; i += blockDim.x)
+            staging[c.offset + i] = to_interchange(c.board[i]);
+    } else {
+        const int64_t rb = c.rows / 64;
+        const int64_t end = min(rb * c.words, (lb + 1) * kCopyTilesPerBlock);
+        for (int64_t t = lb * kCopyTilesPerBlock + threadIdx.x / 32; t < end; t += blockDim.x / 32)
             transpose_tile(c.board, rb, t / rb, t % rb, staging + c.offset, c.words, true, false);
     }
 }
@@ -363,13 +382,14 @@ cudaError_t launch_convert(const uint64_t *src, uint64_t *dst, int64_t n, bool t
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_boards(const CopyDesc *d, int n, const uint64_t *staging, cudaStream_t s) {
-    if (n > 0) scatter_boards_kernel<<<n, kBlock, 0, s>>>(d, staging);
+cudaError_t launch_scatter_boards(const CopyDesc *d, int n, int64_t blocks, const uint64_t *staging,
+                                  cudaStream_t s) {
+    if (n > 0 && blocks > 0) scatter_boards_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(d, n, staging);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_boards(const CopyDesc *d, int n, uint64_t *staging, cudaStream_t s) {
-    if (n > 0) gather_boards_kernel<<<n, kBlock, 0, s>>>(d, staging);
+cudaError_t launch_gather_boards(const CopyDesc *d, int n, int64_t blocks, uint64_t *staging, cudaStream_t s) {
+    if (n > 0 && blocks > 0) gather_boards_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(d, n, staging);
     return cudaGetLastError();
 }
 

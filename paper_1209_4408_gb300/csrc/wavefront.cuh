@@ -446,6 +446,188 @@ __device__ __forceinline__ void run_unit_pass(const BoardDesc &bd, const UnitDes
     }
 }
 
+// Variant with skewed stages: stage g > 0 takes the row that stage g - 1
+// produced in the previous iteration (one register pair per stage boundary),
+// so the K stages of an iteration do not depend on one another and their
+// shuffle / funnel-shift / LOP3 chains overlap.  Each stage then delays the
+// stream by two rows instead of one: stage g's output in iteration j is the
+// generation-(g+1) row a - K + j - (2g + 1), the first output row a leaves
+// in iteration 3K - 1, and a pass runs H + 3K - 1 iterations.  Window slots
+// rotate by renaming as in run_unit_pass.
+template <int K, bool TORUS, bool PARTIAL>
+__device__ __forceinline__ void run_unit_pass_skew(const BoardDesc &bd, const UnitDesc &ud,
+                                                   const uint64_t *__restrict__ src,
+                                                   uint64_t *__restrict__ dst, int kk) {
+    constexpr unsigned kFull = 0xffffffffu;
+    constexpr int NOUT = 3 * K - 1;                // first iteration with an output row
+    constexpr int NPRO3 = (NOUT + 2) / 3 * 3;      // guarded iterations (multiple of 3)
+    const int lane = threadIdx.x & 31;
+    const int R = bd.R, W = bd.W;
+
+    // ---- lane geometry -------------------------------------------------
+    int seg = 0, word = 0, west_src = lane, east_src = lane;
+    bool loads = false, stores = false;
+    uint32_t west_mask = ~0u, east_mask = ~0u, lane_mask = ~0u;
+    if (ud.mode == kUnitFull) {
+        seg = lane / W;
+        word = lane - seg * W;
+        if (seg < ud.S) {
+            loads = stores = true;
+            const int base = lane - word;
+            west_src = base + (word == 0 ? W - 1 : word - 1);
+            east_src = base + (word == W - 1 ? 0 : word + 1);
+            if (!TORUS) {
+                if (word == 0) west_mask = 0;
+                if (word == W - 1) east_mask = 0;
+            }
+        } else {
+            seg = 0;
+            word = 0;
+        }
+    } else {
+        int w = ud.w0 - 1 + lane;
+        loads = lane < ud.U + 2;
+        stores = lane >= 1 && lane <= ud.U;
+        if (TORUS) {
+            w = w < 0 ? w + W : (w >= W ? w - W : w);
+        } else if (w < 0 || w >= W) {
+            lane_mask = 0;
+            loads = false;
+            w = 0;
+        }
+        word = loads ? w : 0;
+        west_src = lane == 0 ? 0 : lane - 1;
+        east_src = lane == 31 ? 31 : lane + 1;
+    }
+    const int a = ud.r0 + seg * ud.H;                       // first output row of the segment
+    const int seg_end = min(a + ud.H, ud.r_end);            // one past its last output row
+    const int nmain = ud.H;                                 // output rows per segment
+
+    // ---- input row stream: row (a - K + j) of src ---------------------
+    // (the last K - 1 iterations load rows past the unit's input; on the
+    // torus they wrap, otherwise rows outside the board read as zero)
+    int lrow = a - K;                                       // row of the next load (unwrapped)
+    int lwrap = lrow;                                       // wrapped row
+    if (TORUS) {
+        lwrap %= R;
+        if (lwrap < 0) lwrap += R;
+    }
+    const uint64_t *colp = src + word;
+    auto load_next = [&](uint32_t &lo, uint32_t &hi) {
+        lo = hi = 0;
+        if (TORUS) {
+            if (loads) {
+                const uint2 v = ld_cg_u64(colp + (size_t)lwrap * W);
+                lo = v.x;
+                hi = v.y;
+            }
+            if (++lwrap == R) lwrap = 0;
+        } else {
+            if (loads && lrow >= 0 && lrow < R) {
+                const uint2 v = ld_cg_u64(colp + (size_t)lrow * W);
+                lo = v.x;
+                hi = v.y;
+            }
+        }
+        ++lrow;
+    };
+
+    // ---- pipeline registers ----------------------------------------------
+    uint32_t s0l[3][K], s0h[3][K], s1l[3][K], s1h[3][K], sal[3][K], sah[3][K];
+    uint32_t inl[K], inh[K];                   // inl[g]: stage g - 1's output of the last iteration
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int g = 0; g < K; ++g) s0l[r][g] = s0h[r][g] = s1l[r][g] = s1h[r][g] = sal[r][g] = sah[r][g] = 0;
+#pragma unroll
+    for (int g = 0; g < K; ++g) inl[g] = inh[g] = 0;
+    uint32_t fl[3], fh[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) load_next(fl[u], fh[u]);
+
+    // One iteration j: the gen-0 row (a - K + j) enters stage 0, every stage
+    // g > 0 takes inl/inh[g]; returns the last stage's output, the
+    // generation-kk row a + j - NOUT.  In the prologue (GUARD) stage g only
+    // runs from iteration 3g on, when its input is a row of the unit.
+    auto iterate = [&](uint32_t x0l, uint32_t x0h, int j, auto guard_tag, auto phase_tag) {
+        constexpr bool GUARD = decltype(guard_tag)::value;
+        constexpr int O = decltype(phase_tag)::value, M = (O + 1) % 3, N = (O + 2) % 3;
+        uint32_t outl[K], outh[K];
+#pragma unroll
+        for (int g = 0; g < K; ++g) {
+            outl[g] = outh[g] = 0;
+            if (GUARD && j < 3 * g) continue;               // input of stage g not produced yet
+            const uint32_t xl = g == 0 ? x0l : inl[g], xh = g == 0 ? x0h : inh[g];
+            const uint32_t wh = __shfl_sync(kFull, xh, west_src) & west_mask;
+            const uint32_t el = __shfl_sync(kFull, xl, east_src) & east_mask;
+            const uint32_t Wl = __funnelshift_l(wh, xh, 1);
+            const uint32_t Eh = __funnelshift_r(xl, el, 1);
+            s0l[N][g] = lop3<kXor3>(Wl, xl, xh);
+            s0h[N][g] = lop3<kXor3>(xl, xh, Eh);
+            s1l[N][g] = lop3<kMaj3>(Wl, xl, xh);
+            s1h[N][g] = lop3<kMaj3>(xl, xh, Eh);
+            sal[N][g] = xl;
+            sah[N][g] = xh;
+            uint32_t ol = rule32(s0l[O][g], s1l[O][g], s0l[M][g], s1l[M][g], s0l[N][g], s1l[N][g], sal[M][g]);
+            uint32_t oh = rule32(s0h[O][g], s1h[O][g], s0h[M][g], s1h[M][g], s0h[N][g], s1h[N][g], sah[M][g]);
+            if (PARTIAL && g >= kk) {                       // pass shorter than K: identity stage
+                ol = sal[M][g];
+                oh = sah[M][g];
+            }
+            if (!TORUS) {
+                const bool inside = (unsigned)(a - K + j - 2 * g - 1) < (unsigned)R;
+                ol = inside ? (ol & lane_mask) : 0u;
+                oh = inside ? (oh & lane_mask) : 0u;
+            }
+            outl[g] = ol;
+            outh[g] = oh;
+        }
+#pragma unroll
+        for (int g = 1; g < K; ++g) {
+            inl[g] = outl[g - 1];
+            inh[g] = outh[g - 1];
+        }
+        return make_uint2(outl[K - 1], outh[K - 1]);
+    };
+
+    using P0 = std::integral_constant<int, 0>;
+    using P1 = std::integral_constant<int, 1>;
+    using P2 = std::integral_constant<int, 2>;
+    int orow = a;                                           // row of the next output
+    uint64_t *outp = dst + word;
+    auto emit = [&](uint2 o) {
+        if (stores && orow < seg_end) st_u64(outp + (size_t)orow * W, o.x, o.y);
+        ++orow;
+    };
+#pragma unroll 1
+    for (int j0 = 0; j0 < NPRO3; j0 += 3) {
+        uint32_t xl = fl[0], xh = fh[0];
+        load_next(fl[0], fh[0]);
+        uint2 o = iterate(xl, xh, j0, std::true_type{}, P0{});
+        if (j0 >= NOUT) emit(o);
+        xl = fl[1], xh = fh[1];
+        load_next(fl[1], fh[1]);
+        o = iterate(xl, xh, j0 + 1, std::true_type{}, P1{});
+        if (j0 + 1 >= NOUT) emit(o);
+        xl = fl[2], xh = fh[2];
+        load_next(fl[2], fh[2]);
+        o = iterate(xl, xh, j0 + 2, std::true_type{}, P2{});
+        if (j0 + 2 >= NOUT) emit(o);
+    }
+#pragma unroll 1
+    for (int j0 = NPRO3; j0 < NOUT + nmain; j0 += 3) {
+        uint32_t xl = fl[0], xh = fh[0];
+        load_next(fl[0], fh[0]);
+        emit(iterate(xl, xh, j0, std::false_type{}, P0{}));
+        xl = fl[1], xh = fh[1];
+        load_next(fl[1], fh[1]);
+        emit(iterate(xl, xh, j0 + 1, std::false_type{}, P1{}));
+        xl = fl[2], xh = fh[2];
+        load_next(fl[2], fh[2]);
+        emit(iterate(xl, xh, j0 + 2, std::false_type{}, P2{}));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Scheduler
 // ---------------------------------------------------------------------------
@@ -559,8 +741,11 @@ __device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pa
 #define GOL_MIN_BLOCKS 1
 #endif
 
+// The skewed variant keeps K more register pairs; at K = 6 it is held to
+// six blocks (three warps per scheduler) per SM.
 template <int K, bool TORUS, int VARIANT>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, (K >= 4 && K <= 6) ? GOL_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32,
+                                  (K >= 4 && K <= 6) ? (VARIANT == 2 && GOL_MIN_BLOCKS < 6 ? 6 : GOL_MIN_BLOCKS) : 1)
 persistent_step_kernel(const PersistArgs A) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -599,11 +784,16 @@ persistent_step_kernel(const PersistArgs A) {
                 run_unit_pass_moves<K, TORUS, false>(bd, ud, src, dst, K);
             else
                 run_unit_pass_moves<K, TORUS, true>(bd, ud, src, dst, kk);
-        } else {
+        } else if (VARIANT == 1) {
             if (kk == K)
                 run_unit_pass<K, TORUS, false>(bd, ud, src, dst, K);
             else
                 run_unit_pass<K, TORUS, true>(bd, ud, src, dst, kk);
+        } else {
+            if (kk == K)
+                run_unit_pass_skew<K, TORUS, false>(bd, ud, src, dst, K);
+            else
+                run_unit_pass_skew<K, TORUS, true>(bd, ud, src, dst, kk);
         }
         // every lane's stores of this pass are ordered before the counter
         // updates that publish it (acquire-release fence, then the warp barrier)
@@ -622,11 +812,16 @@ cudaError_t launch_persistent_impl(const PersistArgs &a, bool torus, int variant
             persistent_step_kernel<K, true, 0><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
         else
             persistent_step_kernel<K, false, 0><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
-    } else {
+    } else if (variant == 1) {
         if (torus)
             persistent_step_kernel<K, true, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
         else
             persistent_step_kernel<K, false, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+    } else {
+        if (torus)
+            persistent_step_kernel<K, true, 2><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+        else
+            persistent_step_kernel<K, false, 2><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
@@ -637,8 +832,11 @@ cudaError_t persistent_occupancy_impl(bool torus, int variant, int *bps) {
     if (variant == 0)
         return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, 0>, t, 0)
                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, 0>, t, 0);
-    return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, 1>, t, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, 1>, t, 0);
+    if (variant == 1)
+        return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, 1>, t, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, 1>, t, 0);
+    return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, 2>, t, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, 2>, t, 0);
 }
 
 #define GOL_INSTANTIATE_PERSISTENT(KV)                                                             \

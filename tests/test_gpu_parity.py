@@ -126,16 +126,22 @@ def test_packed_all_512_neighbourhoods(gol, R, C):
 ])
 def test_packed_random_shapes(gol, opts, R, C, torus):
     cells = synth.bernoulli_board(R, C, 0.37, 1000 * R + C)
-    for k, rows in [(1, 0), (4, 3), (8, 0), (16, 64)]:
-        opts(k, rows)
-        for gens in (1, 5, 19):
-            assert_same(run_gpu(gol, cells, gens, torus), oracle.run(cells, gens, torus),
-                        "%dx%d torus=%s K=%d rows=%d gens=%d" % (R, C, torus, k, rows, gens))
+    try:
+        for variant in (-1, 0, 2):
+            gol.gol_set_option(gol.GOL_OPT_PIPELINE, variant)
+            for k, rows in [(1, 0), (4, 3), (8, 0), (16, 64)]:
+                opts(k, rows)
+                for gens in (1, 5, 19):
+                    assert_same(run_gpu(gol, cells, gens, torus), oracle.run(cells, gens, torus),
+                                "%dx%d torus=%s K=%d rows=%d gens=%d variant=%d" % (R, C, torus, k, rows, gens,
+                                                                                   variant))
+    finally:
+        gol.gol_set_option(gol.GOL_OPT_PIPELINE, -1)
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 8, 16])
 @pytest.mark.parametrize("rows", [1, 8, 64, 1000])
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_packed_result_independent_of_pass_and_tile(gol, opts, k, rows, variant):
     R, C, G = 192, 2240, 23
     cells = synth.bernoulli_board(R, C, 0.5, 4242)
@@ -149,7 +155,7 @@ def test_packed_result_independent_of_pass_and_tile(gol, opts, k, rows, variant)
         assert_same(run_gpu(gol, cells2, G, torus=False), oracle.run(cells2, G, torus=False),
                     "bounded K=%d rows=%d variant=%d" % (k, rows, variant))
     finally:
-        gol.gol_set_option(gol.GOL_OPT_PIPELINE, 0)
+        gol.gol_set_option(gol.GOL_OPT_PIPELINE, -1)
 
 
 def test_packed_split_runs_compose(gol):
