@@ -113,7 +113,7 @@ int gol_get_region(gol_handle h, int64_t r0, int64_t c0, int64_t nr, int64_t nc,
  *   stream   the cudaStream_t to run on (null = default stream).
  * rows >= 1, cols a multiple of 64 and at most 30*4096*64 = 7864320,
  * generations >= 0.  The call allocates nothing: the scheduler's workspace
- * is a file-scope device array of about 1.3 MiB that every GPU loading the
+ * is a file-scope device array of about 1.8 MiB that every GPU loading the
  * library holds until the process exits.  The first call on a device looks
  * up that array's device address; make it before any stream capture.  All
  * calls share the array and it keeps the last call's contents (every call

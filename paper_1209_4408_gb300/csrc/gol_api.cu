@@ -449,10 +449,11 @@ int build_plan(Plan &P) {
         return fail(GOL_EINVAL, "batch too large for one launch (%lld tasks)", (long long)P.total_tasks);
     const size_t nb = P.boards.size(), nu = P.units.size();
     const int64_t max_blocks = (int64_t)g_dev.sms * std::max(1, bps);
-    // device memory: boards | units | next_pass | join | ctr | ring
+    // device memory: boards | units | run | next_pass | join | ctr | ring
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t o_units = al(nb * sizeof(BoardDesc));
-    const size_t o_next = o_units + al(nu * sizeof(UnitDesc));
+    const size_t o_run = o_units + al(nu * sizeof(UnitDesc));
+    const size_t o_next = o_run + al(nu * sizeof(UnitRun));
     const size_t o_join = o_next + al(nu * 4);
     const size_t o_ctr = o_join + al(2 * nu * 4);
     const size_t o_ring = o_ctr + al((4 + nb) * 4);
@@ -468,6 +469,7 @@ int build_plan(Plan &P) {
     PersistArgs &a = P.args;
     a.boards = (const BoardDesc *)base;
     a.units = (const UnitDesc *)(base + o_units);
+    a.run = (UnitRun *)(base + o_run);
     a.next_pass = (int32_t *)(base + o_next);
     a.join = (int32_t *)(base + o_join);
     a.ctr = (int32_t *)(base + o_ctr);
@@ -1235,6 +1237,7 @@ int gol_debug_unfilled_wait(int64_t timeout_ms) {
     char *base = (char *)ws.p;
     a.boards = nullptr;
     a.units = nullptr;
+    a.run = nullptr;
     a.next_pass = (int32_t *)(base + 0);
     a.join = (int32_t *)(base + 256);
     a.ctr = (int32_t *)(base + 512);
@@ -1269,12 +1272,13 @@ namespace {
 constexpr int kStaticMaxUnits = 4096;          // units of one board
 constexpr int kStaticMaxTasks = 1 << 18;       // queue slots per launch
 constexpr size_t kSaUnits = 256;               // offsets in the static workspace
-constexpr size_t kSaNext = kSaUnits + sizeof(UnitDesc) * kStaticMaxUnits;
+constexpr size_t kSaRun = kSaUnits + sizeof(UnitDesc) * kStaticMaxUnits;
+constexpr size_t kSaNext = kSaRun + sizeof(UnitRun) * kStaticMaxUnits;
 constexpr size_t kSaJoin = kSaNext + 4 * (size_t)kStaticMaxUnits;
 constexpr size_t kSaCtr = kSaJoin + 8 * (size_t)kStaticMaxUnits;
 constexpr size_t kSaStatus = kSaCtr + 256;     // [0] status, [1] current buffer
 constexpr size_t kSaRing = kSaStatus + 256;
-constexpr size_t kStaticBytes = kSaRing + 4 * (size_t)kStaticMaxTasks;   // about 1.3 MiB
+constexpr size_t kStaticBytes = kSaRing + 4 * (size_t)kStaticMaxTasks;   // about 1.8 MiB
 
 // Shared by every call on a device and kept until the process exits.
 static __device__ __align__(256) unsigned char g_static_workspace[kStaticBytes];
@@ -1339,6 +1343,7 @@ extern "C" int gol_step_packed_noalloc(uint64_t *d_board, uint64_t *d_spare, int
     PersistArgs a{};
     a.boards = (const BoardDesc *)base;
     a.units = (const UnitDesc *)(base + kSaUnits);
+    a.run = (UnitRun *)(base + kSaRun);
     a.next_pass = (int32_t *)(base + kSaNext);
     a.join = (int32_t *)(base + kSaJoin);
     a.ctr = (int32_t *)(base + kSaCtr);

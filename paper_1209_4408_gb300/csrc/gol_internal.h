@@ -63,11 +63,27 @@ struct UnitDesc {
     int32_t pad;
 };
 
+// What a warp needs to run a pass of one unit, in one 128-byte record:
+// the unit's geometry, its board's fields and the board's current buffer at
+// the start of the launch (a board's `cur` only changes after all its units
+// have run their last pass).  Written by sched_init_kernel at the start of
+// every launch from the unit and board tables.
+struct __align__(128) UnitRun {
+    uint64_t *buf[2];
+    int32_t *curp;     // the board's device `cur`
+    int32_t board, R, W, npass, gens, nunits, cur;
+    int32_t r0, r_end, H, S, w0, U, mode, nnb;
+    int32_t nb[kMaxNeighbours];
+    int32_t pad[3];
+};
+static_assert(sizeof(UnitRun) == 128, "UnitRun is one 128-byte line");
+
 // Kernel arguments of the persistent dataflow kernel.
 struct PersistArgs {
     const BoardDesc *boards;
     const UnitDesc *units;
-    int32_t *next_pass; // [nunits] the pass each unit runs next (set when it is claimed)
+    UnitRun *run;       // [nunits] per-launch unit records (sched_init_kernel)
+    int32_t *next_pass; // [nunits] the pass a queued unit runs next (set when it is claimed)
     int32_t *join;      // [2 * nunits] join counters, one per pass parity
     int32_t *ring;      // [total_tasks] work queue, -1 = empty slot
     int32_t *ctr;       // [0] head ticket, [1] tail slot, [2] tasks completed, [3] status,

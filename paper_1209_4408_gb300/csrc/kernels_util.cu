@@ -22,9 +22,33 @@ __global__ void sched_init_kernel(PersistArgs a, int nboards) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (i < a.nunits) {
+            const UnitDesc u = a.units[i];
+            const BoardDesc b = a.boards[u.board];
+            UnitRun r;
+            r.buf[0] = b.buf[0];
+            r.buf[1] = b.buf[1];
+            r.curp = b.cur;
+            r.board = u.board;
+            r.R = b.R;
+            r.W = b.W;
+            r.npass = b.npass;
+            r.gens = b.gens;
+            r.nunits = b.nunits;
+            r.cur = *b.cur;
+            r.r0 = u.r0;
+            r.r_end = u.r_end;
+            r.H = u.H;
+            r.S = u.S;
+            r.w0 = u.w0;
+            r.U = u.U;
+            r.mode = u.mode;
+            r.nnb = u.nnb;
+            for (int k = 0; k < kMaxNeighbours; ++k) r.nb[k] = u.nb[k];
+            r.pad[0] = r.pad[1] = r.pad[2] = 0;
+            a.run[i] = r;
             a.next_pass[i] = 1;            // every unit's first pass is queued below
-            a.join[2 * i] = 0;     // join counters of both pass parities
-            a.join[2 * i + 1] = 0;
+            a.join[2 * i] = u.nnb + 1;     // join counters of both pass parities count down
+            a.join[2 * i + 1] = u.nnb + 1; // the completions a pass waits for
         }
         if (i < a.total_tasks) a.ring[i] = i < a.nunits ? (int32_t)i : -1;
         if (i < nboards) a.ctr[4 + i] = 0;

@@ -44,6 +44,11 @@
 
 #include "gol_internal.h"
 
+// 1: the guarded prologue iterations of a pass are unrolled completely.
+#ifndef GOL_UNROLL_PROLOGUE
+#define GOL_UNROLL_PROLOGUE 1
+#endif
+
 namespace gol {
 
 template <unsigned LUT>
@@ -105,14 +110,14 @@ __device__ __forceinline__ void st_u64(uint64_t *p, uint32_t lo, uint32_t hi) {
 // Variant of run_unit_pass whose three-row window shifts by register moves
 // (iteration loop unrolled twice); fewer registers, more issue slots.
 template <int K, bool TORUS, bool PARTIAL>
-__device__ __forceinline__ void run_unit_pass_moves(const BoardDesc &bd, const UnitDesc &ud,
+__device__ __forceinline__ void run_unit_pass_moves(const UnitRun &ud,
                                               const uint64_t *__restrict__ src,
                                               uint64_t *__restrict__ dst, int kk) {
     constexpr unsigned kFull = 0xffffffffu;
     constexpr int PF = 2;                          // rows prefetched ahead (2K is a multiple)
     constexpr int NPRO = 2 * K;                    // prologue iterations
     const int lane = threadIdx.x & 31;
-    const int R = bd.R, W = bd.W;
+    const int R = ud.R, W = ud.W;
 
     // ---- lane geometry -------------------------------------------------
     int seg = 0, word = 0, west_src = lane, east_src = lane;
@@ -271,14 +276,14 @@ __device__ __forceinline__ void run_unit_pass_moves(const BoardDesc &bd, const U
 
 // Variant whose window slots rotate by renaming (loop unrolled three times).
 template <int K, bool TORUS, bool PARTIAL>
-__device__ __forceinline__ void run_unit_pass(const BoardDesc &bd, const UnitDesc &ud,
+__device__ __forceinline__ void run_unit_pass(const UnitRun &ud,
                                               const uint64_t *__restrict__ src,
                                               uint64_t *__restrict__ dst, int kk) {
     constexpr unsigned kFull = 0xffffffffu;
     constexpr int NPRO = 2 * K;                    // iterations before the first output row
     constexpr int NPRO3 = (NPRO + 2) / 3 * 3;      // guarded iterations (multiple of 3)
     const int lane = threadIdx.x & 31;
-    const int R = bd.R, W = bd.W;
+    const int R = ud.R, W = ud.W;
 
     // ---- lane geometry -------------------------------------------------
     int seg = 0, word = 0, west_src = lane, east_src = lane;
@@ -416,8 +421,14 @@ __device__ __forceinline__ void run_unit_pass(const BoardDesc &bd, const UnitDes
         ++orow;
     };
     // prologue: the first 2K iterations (rounded up to a multiple of 3) with
-    // guards; iterations from 2K on already produce output rows
+    // guards; iterations from 2K on already produce output rows.  Unrolled
+    // completely, the guards are known at compile time and the partial
+    // stages of successive iterations overlap.
+#if GOL_UNROLL_PROLOGUE
+#pragma unroll
+#else
 #pragma unroll 1
+#endif
     for (int j0 = 0; j0 < NPRO3; j0 += 3) {
         uint32_t xl = fl[0], xh = fh[0];
         load_next(fl[0], fh[0]);
@@ -455,14 +466,14 @@ __device__ __forceinline__ void run_unit_pass(const BoardDesc &bd, const UnitDes
 // in iteration 3K - 1, and a pass runs H + 3K - 1 iterations.  Window slots
 // rotate by renaming as in run_unit_pass.
 template <int K, bool TORUS, bool PARTIAL>
-__device__ __forceinline__ void run_unit_pass_skew(const BoardDesc &bd, const UnitDesc &ud,
+__device__ __forceinline__ void run_unit_pass_skew(const UnitRun &ud,
                                                    const uint64_t *__restrict__ src,
                                                    uint64_t *__restrict__ dst, int kk) {
     constexpr unsigned kFull = 0xffffffffu;
     constexpr int NOUT = 3 * K - 1;                // first iteration with an output row
     constexpr int NPRO3 = (NOUT + 2) / 3 * 3;      // guarded iterations (multiple of 3)
     const int lane = threadIdx.x & 31;
-    const int R = bd.R, W = bd.W;
+    const int R = ud.R, W = ud.W;
 
     // ---- lane geometry -------------------------------------------------
     int seg = 0, word = 0, west_src = lane, east_src = lane;
@@ -599,7 +610,11 @@ __device__ __forceinline__ void run_unit_pass_skew(const BoardDesc &bd, const Un
         if (stores && orow < seg_end) st_u64(outp + (size_t)orow * W, o.x, o.y);
         ++orow;
     };
+#if GOL_UNROLL_PROLOGUE
+#pragma unroll
+#else
 #pragma unroll 1
+#endif
     for (int j0 = 0; j0 < NPRO3; j0 += 3) {
         uint32_t xl = fl[0], xh = fh[0];
         load_next(fl[0], fh[0]);
@@ -631,8 +646,8 @@ __device__ __forceinline__ void run_unit_pass_skew(const BoardDesc &bd, const Un
 // ---------------------------------------------------------------------------
 // Scheduler
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int pass_gens(const BoardDesc &bd, int pass) {
-    const int base = bd.gens / bd.npass, rem = bd.gens - base * bd.npass;
+__device__ __forceinline__ int pass_gens(const UnitRun &r, int pass) {
+    const int base = r.gens / r.npass, rem = r.gens - base * r.npass;
     return base + (pass <= rem ? 1 : 0);
 }
 
@@ -658,7 +673,7 @@ static __device__ int wait_for_slot(const PersistArgs &A, int t) {
             return -1;
         }
         __nanosleep(ns);
-        if (ns < 1024) ns <<= 1;
+        if (ns < 256) ns <<= 1;
     }
     atomicCAS(&A.ctr[3], 0, GOL_ETIMEOUT);
     atomicCAS(A.sticky, 0, GOL_ETIMEOUT);
@@ -690,48 +705,46 @@ __device__ __forceinline__ int atom_add_acq_rel(int32_t *p, int v) {
 // the pass already ordered by an acquire-release fence and a warp barrier.
 //
 // Join counters: unit v may run pass q+1 once v and each of its nnb(v)
-// neighbours have finished pass q.  Every finisher of pass q adds one to
-// join[v][q & 1] for itself and each of its neighbours (the relation is
-// symmetric); the add that brings the counter to nnb(v) + 1 makes v ready,
-// and only that one thread sees it, so v is claimed exactly once.  The
-// claimer resets the counter before v can run again, and a neighbour is
-// never more than one pass ahead of v, so two parities suffice.  Lane i
-// handles candidate i (u itself, then its neighbours); the first ready lane
-// continues in this warp, the others go to the queue.  Returns the unit
-// this warp runs next or -1.
-__device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pass, const UnitDesc &ud,
-                                             const BoardDesc &bd) {
+// neighbours have finished pass q.  join[v][q & 1] starts at nnb(v) + 1 and
+// every finisher of pass q subtracts one for itself and for each of its
+// neighbours (the relation is symmetric); the subtraction that reaches zero
+// makes v ready, and only that one thread sees it, so v is claimed exactly
+// once.  v restores the counter to nnb(v) + 1 when it starts pass q+1:
+// nothing else touches that counter until v and its neighbours finish pass
+// q+2, which needs v's pass q+1, so two parities suffice.  Lane 0 handles u
+// itself and lane i its neighbour i - 1 (`my_nb`); the first ready lane's
+// unit continues in this warp (at pass + 1, on the same board), the others
+// are written their pass and go to the queue.  Returns the unit this warp
+// runs next or -1.
+__device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pass, const UnitRun &r, int my_nb) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int npass = bd.npass;
     if (lane == 0) {
         red_add(&A.ctr[2], 1);
-        if (pass == npass) {
+        if (pass == r.npass) {
             // last unit of the board to finish flips the board's current buffer
-            if (atomicAdd(&A.ctr[4 + ud.board], 1) == bd.nunits - 1) {
-                if (npass & 1) *bd.cur ^= 1;
-                A.ctr[4 + ud.board] = 0;
+            if (atomicAdd(&A.ctr[4 + r.board], 1) == r.nunits - 1) {
+                if (r.npass & 1) *r.curp ^= 1;
+                A.ctr[4 + r.board] = 0;
             }
         }
     }
-    if (pass >= npass) return -1;            // no unit of this board runs again
-    if (ud.nnb == 0) return u;               // a board of one unit waits for nobody
+    if (pass >= r.npass) return -1;            // no unit of this board runs again
+    if (r.nnb == 0) return u;                  // a board of one unit waits for nobody
     int v = -1;
     bool ready = false;
-    if (lane <= ud.nnb) {
-        v = lane == 0 ? u : A.units[u].nb[lane - 1];
-        int32_t *j = &A.join[2 * v + (pass & 1)];
-        if (atom_add_acq_rel(j, 1) == A.units[v].nnb) {
-            *j = 0;
-            A.next_pass[v] = pass + 1;            // the pass v runs next
-            ready = true;
-        }
+    if (lane <= r.nnb) {
+        v = lane == 0 ? u : my_nb;
+        ready = atom_add_acq_rel(&A.join[2 * v + (pass & 1)], -1) == 1;
     }
     const unsigned mask = __ballot_sync(kFull, ready);
     if (!mask) return -1;
     const int leader = __ffs(mask) - 1;
     const int next = __shfl_sync(kFull, v, leader);
-    if (ready && lane != leader) enqueue(A, v);
+    if (ready && lane != leader) {
+        A.next_pass[v] = pass + 1;            // published by the queue slot's release
+        enqueue(A, v);
+    }
     return next;
 }
 
@@ -749,8 +762,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32,
 persistent_step_kernel(const PersistArgs A) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    int u = -1, pass = 0, cur = 0;
-    bool same = false;   // continuing with the unit just run: pass and buffer known
+    int u = -1, pass = 0;
     for (;;) {
         if (u < 0) {
             int t = 0;
@@ -758,50 +770,48 @@ persistent_step_kernel(const PersistArgs A) {
             t = __shfl_sync(kFull, t, 0);
             if (t >= A.total_tasks) return;
             int v = -1;
-            if (lane == 0) v = wait_for_slot(A, t);
+            if (lane == 0) {
+                v = wait_for_slot(A, t);
+                // written before the slot by the thread that claimed v; the
+                // slot's acquire load orders this read after it
+                if (v >= 0) pass = A.next_pass[v];
+            }
             v = __shfl_sync(kFull, v, 0);
             if (v < 0) return;
-            u = v;
-            same = false;
-        }
-        const UnitDesc ud = A.units[u];
-        const BoardDesc bd = A.boards[ud.board];
-        if (same) {
-            ++pass;          // a board's buffer index only changes after its last pass
-        } else {
-            if (lane == 0) {
-                pass = ld_acquire(&A.next_pass[u]);   // written by the thread that made u ready
-                cur = ld_acquire(bd.cur);
-            }
             pass = __shfl_sync(kFull, pass, 0);
-            cur = __shfl_sync(kFull, cur, 0);
+            u = v;
+        } else {
+            ++pass;          // continuing in this warp: the next pass of a unit of the same board
         }
-        const uint64_t *src = bd.buf[(cur + pass - 1) & 1];
-        uint64_t *dst = bd.buf[(cur + pass) & 1];
-        const int kk = pass_gens(bd, pass);
+        const UnitRun r = A.run[u];
+        const int my_nb = (lane >= 1 && lane <= kMaxNeighbours) ? A.run[u].nb[lane - 1] : u;
+        // restore the join counter that made u ready (see complete_pass)
+        if (lane == 0 && pass > 1) A.join[2 * u + ((pass - 1) & 1)] = r.nnb + 1;
+        const uint64_t *src = r.buf[(r.cur + pass - 1) & 1];
+        uint64_t *dst = r.buf[(r.cur + pass) & 1];
+        const int kk = pass_gens(r, pass);
         if (VARIANT == 0) {
             if (kk == K)
-                run_unit_pass_moves<K, TORUS, false>(bd, ud, src, dst, K);
+                run_unit_pass_moves<K, TORUS, false>(r, src, dst, K);
             else
-                run_unit_pass_moves<K, TORUS, true>(bd, ud, src, dst, kk);
+                run_unit_pass_moves<K, TORUS, true>(r, src, dst, kk);
         } else if (VARIANT == 1) {
             if (kk == K)
-                run_unit_pass<K, TORUS, false>(bd, ud, src, dst, K);
+                run_unit_pass<K, TORUS, false>(r, src, dst, K);
             else
-                run_unit_pass<K, TORUS, true>(bd, ud, src, dst, kk);
+                run_unit_pass<K, TORUS, true>(r, src, dst, kk);
         } else {
             if (kk == K)
-                run_unit_pass_skew<K, TORUS, false>(bd, ud, src, dst, K);
+                run_unit_pass_skew<K, TORUS, false>(r, src, dst, K);
             else
-                run_unit_pass_skew<K, TORUS, true>(bd, ud, src, dst, kk);
+                run_unit_pass_skew<K, TORUS, true>(r, src, dst, kk);
         }
-        // every lane's stores of this pass are ordered before the counter
-        // updates that publish it (acquire-release fence, then the warp barrier)
+        // every lane's stores of this pass (and the counter reset) are ordered
+        // before the counter updates that publish it (acquire-release fence,
+        // then the warp barrier)
         fence_acq_rel_gpu();
         __syncwarp();
-        const int next = complete_pass(A, u, pass, ud, bd);
-        same = next == u;
-        u = next;
+        u = complete_pass(A, u, pass, r, my_nb);
     }
 }
 
