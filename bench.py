@@ -54,6 +54,9 @@ def parse():
                     help="requests of the served run added to the batch line (0 = skip)")
     ap.add_argument("--serve-load", type=float, default=0.7,
                     help="offered load of the served run as a fraction of the measured batched GCUPS")
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="also serve the stream at offered loads 0.3 / 0.7 / 1.0 and at 0.7 under a 32 MiB "
+                         "budget (about half the boards the unconstrained run holds at its peak)")
     ap.add_argument("--fcfs-requests", type=int, default=24,
                     help="requests of the same trace served one at a time (baseline)")
     return ap.parse_args()
@@ -416,6 +419,14 @@ def run_gpu(args, rank, world, local):
     if args.workload == "batch" and args.serve_requests > 0:
         out["served"] = served_run(gol, args.serve_requests, args.serve_load, value / world, 120 << 30,
                                    args.fcfs_requests)
+        if args.serve_sweep:
+            keys = ("offered_load", "budget_bytes", "requests", "p50_ms", "p99_ms", "mean_ms", "gcups",
+                    "max_active", "max_waiting", "peak_device_bytes")
+            sweep = []
+            for load, budget in ((0.3, 120 << 30), (0.7, 120 << 30), (1.0, 120 << 30), (0.7, 32 << 20)):
+                r = served_run(gol, args.serve_requests, load, value / world, budget, 0)
+                sweep.append({k: r[k] for k in keys if k in r})
+            out["served_sweep"] = sweep
     gol.gol_set_allocator(None, None)
     if rank == 0:
         if not args.no_cpu:

@@ -652,7 +652,9 @@ __device__ __forceinline__ int pass_gens(const UnitRun &r, int pass) {
 }
 
 // Lane 0: wait for queue slot t.  Returns the unit id, or -1 when all work
-// is done or the launch failed (status set).
+// is done or the launch failed (status set).  The slot is polled with one
+// acquire load per round; the launch status, the completion count and the
+// clock are checked every eighth round.
 static __device__ int wait_for_slot(const PersistArgs &A, int t) {
     uint64_t t_last = global_ns();
     int seen = ld_acquire(&A.ctr[2]);
@@ -660,20 +662,22 @@ static __device__ int wait_for_slot(const PersistArgs &A, int t) {
     for (long long spin = 0; spin < (1ll << 32); ++spin) {
         const int v = ld_acquire(&A.ring[t]);
         if (v >= 0) return v;
-        if (ld_acquire(&A.ctr[3]) != 0) return -1;
-        const int c = ld_acquire(&A.ctr[2]);
-        if (c >= A.total_tasks) return -1;
-        const uint64_t now = global_ns();
-        if (c != seen) {
-            seen = c;
-            t_last = now;
-        } else if (now - t_last > (uint64_t)A.timeout_ns) {
-            atomicCAS(&A.ctr[3], 0, GOL_ETIMEOUT);
-            atomicCAS(A.sticky, 0, GOL_ETIMEOUT);
-            return -1;
+        if ((spin & 7) == 7) {
+            if (ld_acquire(&A.ctr[3]) != 0) return -1;
+            const int c = ld_acquire(&A.ctr[2]);
+            if (c >= A.total_tasks) return -1;
+            const uint64_t now = global_ns();
+            if (c != seen) {
+                seen = c;
+                t_last = now;
+            } else if (now - t_last > (uint64_t)A.timeout_ns) {
+                atomicCAS(&A.ctr[3], 0, GOL_ETIMEOUT);
+                atomicCAS(A.sticky, 0, GOL_ETIMEOUT);
+                return -1;
+            }
         }
         __nanosleep(ns);
-        if (ns < 256) ns <<= 1;
+        if (ns < 128) ns <<= 1;
     }
     atomicCAS(&A.ctr[3], 0, GOL_ETIMEOUT);
     atomicCAS(A.sticky, 0, GOL_ETIMEOUT);
