@@ -342,8 +342,12 @@ def run_gpu(args, rank, world, local):
     e2e = None
     if not args.no_e2e:
         e2e_steps = max(1, min(args.steps, 3))
-        out_pinned = torch.empty_like(pinned) if pinned is not None else None
+        out_pinned = torch.empty(pinned.numel(), dtype=pinned.dtype, pin_memory=True) if pinned is not None else None
         host_out = out_pinned.numpy().view(np.uint64) if out_pinned is not None else None
+        if layout == gol.GOL_LAYOUT_PACKED:
+            # warm-up of the transfer path (staging buffers come from the caching allocator)
+            gol.gol_set_packed_batch(handles, host)
+            gol.gol_get_packed_batch(handles, host_out)
         barrier()
         t0 = time.perf_counter()
         h2d = d2h = 0
