@@ -291,11 +291,13 @@ def run_gpu(args, rank, world, local):
             b.set(synth.bernoulli_board(s.rows, s.cols, s.density, s.seed))
             boards.append(b)
     handles = [b.handle for b in boards]
+    handle_array = np.array(handles, dtype=np.uint64)   # built once, as a caller moving a batch every step would
     gens = [s.gens for s in specs]
+    gens_array = np.array(gens, dtype=np.int64)
     torch.cuda.synchronize()
 
     def step():
-        gol.gol_step_batch(handles, gens)
+        gol.gol_step_batch(handle_array, gens_array)
 
     # ---- device-resident timing ------------------------------------------------
     for _ in range(args.warmup):
@@ -346,8 +348,8 @@ def run_gpu(args, rank, world, local):
         host_out = out_pinned.numpy().view(np.uint64) if out_pinned is not None else None
         if layout == gol.GOL_LAYOUT_PACKED:
             # warm-up of the transfer path (staging buffers come from the caching allocator)
-            gol.gol_set_packed_batch(handles, host)
-            gol.gol_get_packed_batch(handles, host_out)
+            gol.gol_set_packed_batch(handle_array, host)
+            gol.gol_get_packed_batch(handle_array, host_out)
         barrier()
         t0 = time.perf_counter()
         h2d = d2h = 0
@@ -356,14 +358,14 @@ def run_gpu(args, rank, world, local):
             if layout == gol.GOL_LAYOUT_PACKED:
                 # one upload of all boards, the step, one download of all boards
                 ta = time.perf_counter()
-                gol.gol_set_packed_batch(handles, host)
+                gol.gol_set_packed_batch(handle_array, host)
                 torch.cuda.synchronize()
                 tb = time.perf_counter()
                 h2d += host.nbytes
                 step()
                 torch.cuda.synchronize()
                 tc = time.perf_counter()
-                gol.gol_get_packed_batch(handles, host_out)
+                gol.gol_get_packed_batch(handle_array, host_out)
                 d2h += host_out.nbytes
                 td = time.perf_counter()
                 phase["upload_s"] += tb - ta

@@ -92,7 +92,10 @@ int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords);
  * (handles must be distinct; generation counters reset to 0; asynchronous
  * when `words` is pinned).  gol_get_packed_batch gathers the boards'
  * current states into one device buffer, copies it to `words` and
- * synchronises.  Non-packed boards are GOL_EINVAL. */
+ * synchronises.  When `words` is page-locked memory registered with CUDA
+ * (cudaHostAlloc, cudaHostRegister) the scatter / gather kernel reads or
+ * writes it in place, with no staging copy (GOL_OPT_ZERO_COPY = 0 turns
+ * that off); pageable memory is staged.  Non-packed boards are GOL_EINVAL. */
 int gol_set_packed_batch(const gol_handle *hs, size_t n, const uint64_t *words, size_t nwords);
 int gol_get_packed_batch(const gol_handle *hs, size_t n, uint64_t *words, size_t nwords);
 
@@ -199,6 +202,14 @@ const char *gol_last_error(void);
  *                          (stage g works one row behind stage g - 1, so the
  *                          stages of a row step are independent), -1
  *                          (default) = 1; results are identical
+ *   GOL_OPT_ZERO_COPY      1 (default): many-board transfers read and write
+ *                          pinned host buffers in place; 0: always through a
+ *                          device staging buffer and cudaMemcpyAsync
+ *   GOL_OPT_BYTE_CLUSTER   1 (default): a byte board whose rows fit the
+ *                          shared memory of one thread-block cluster (8 CTAs,
+ *                          2 x ceil(rows / 8) x cols <= 227 KiB) runs all its
+ *                          generations in one launch of that cluster; 0: one
+ *                          launch per generation (graph replay when long)
  * Unknown keys or values are GOL_EINVAL. */
 #define GOL_OPT_GENS_PER_PASS 1
 #define GOL_OPT_TILE_ROWS 2
@@ -207,6 +218,8 @@ const char *gol_last_error(void);
 #define GOL_OPT_ORIENTATION 5
 #define GOL_OPT_CHAIN_PERMILLE 6
 #define GOL_OPT_PIPELINE 7
+#define GOL_OPT_ZERO_COPY 8
+#define GOL_OPT_BYTE_CLUSTER 9
 int gol_set_option(int key, int64_t value);
 int gol_get_option(int key, int64_t *value);
 

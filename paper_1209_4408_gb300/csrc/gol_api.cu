@@ -79,6 +79,8 @@ void *g_alloc_ctx = nullptr;
 int64_t g_opt_k = 0, g_opt_rows = 0, g_opt_graphs = 1, g_opt_timeout_ms = 5000, g_opt_orient = 0;
 int64_t g_opt_chain = 0;     // chain cap, per mille of the average work per warp slot (0 = auto)
 int64_t g_opt_variant = -1;  // step kernel variant (see launch_persistent), -1 = default
+int64_t g_opt_zero_copy = 1; // many-board transfers read / write pinned host buffers in place
+int64_t g_opt_byte_cluster = 1; // byte boards that fit one cluster's shared memory step there
 uint64_t g_serial = 0;
 
 struct DeviceState {
@@ -633,7 +635,23 @@ int run_packed(const std::vector<gol_handle> &hs, const std::vector<int64_t> &ge
 // starting buffer is kept with the board.
 constexpr int kByteGraphGens = 64;
 
+// Boards that fit the shared memory of one thread-block cluster run all
+// their generations inside one launch (at most this many per launch).
+constexpr int kByteClusterGensPerLaunch = 1 << 14;
+
 int step_bytes(gol_handle h, int64_t G) {
+    if (g_opt_byte_cluster && G > 0 && byte_cluster_size(h->rows, h->cols) > 0) {
+        while (G > 0) {
+            const int g = (int)std::min<int64_t>(G, kByteClusterGensPerLaunch);
+            cudaError_t e = launch_byte_cluster((const uint8_t *)h->buf[h->cur], (uint8_t *)h->buf[h->cur ^ 1], h->rows,
+                                                h->cols, h->torus, g, g_stream);
+            if (e != cudaSuccess) return cuda_fail(e, "byte cluster launch");
+            h->cur ^= 1;
+            h->generation += g;
+            G -= g;
+        }
+        return GOL_OK;
+    }
     if (g_opt_graphs && g_stream != nullptr && G >= 2 * kByteGraphGens) {
         if (h->byte_graph_stream != g_stream) {
             for (auto &ge : h->byte_graph)
@@ -905,35 +923,105 @@ int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords) {
 
 namespace {
 // shared checks of the many-board transfers; fills descriptors and offsets
-int many_plan(const gol_handle *hs, size_t n, size_t nwords, std::vector<CopyDesc> &d, bool scatter,
-              int64_t &blocks) {
+// Many-board transfer plans, cached by handle list (a batch moved every step
+// reuses its plan): the boards' copy descriptors and the copy grid's
+// block-to-board table, in device memory.  Descriptors name both buffers
+// and the device `cur` of a board, so they stay valid while it is stepped.
+struct CopyPlan {
+    std::vector<gol_handle> hs;
+    std::vector<uint64_t> serials;
+    int64_t nwords = 0, blocks = 0;
+    bool distinct = true;
+    std::vector<CopyDesc> d;           // host copies of what dmem holds
+    std::vector<int32_t> bb;
+    void *dmem = nullptr;              // CopyDesc[n] | int32 block_board[blocks]
+    size_t board_off = 0;
+    void (*free_fn)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+    const CopyDesc *desc() const { return (const CopyDesc *)dmem; }
+    const int32_t *block_board() const { return (const int32_t *)((const char *)dmem + board_off); }
+    ~CopyPlan() {
+        if (dmem) {
+            if (!free_fn) cudaStreamSynchronize(g_stream);
+            dev_free(dmem, free_fn, alloc_ctx);
+        }
+    }
+};
+// heap-allocated and never destroyed, like the step plans (see g_plans)
+std::vector<std::unique_ptr<CopyPlan>> &g_copy_plans = *new std::vector<std::unique_ptr<CopyPlan>>();
+constexpr size_t kMaxCopyPlans = 8;
+
+int copy_plan(const gol_handle *hs, size_t n, const CopyPlan **out) {
     if (!hs) return fail(GOL_EINVAL, "null handle array");
     if (n > (size_t)(1 << 30)) return fail(GOL_EINVAL, "too many boards");
+    for (size_t i = 0; i < n; ++i) {
+        if (!valid(hs[i])) return fail(GOL_EINVAL, "invalid handle at %zu", i);
+        if (hs[i]->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board %zu is not packed", i);
+    }
+    for (size_t k = 0; k < g_copy_plans.size(); ++k) {
+        const CopyPlan &P = *g_copy_plans[k];
+        if (P.hs.size() != n || !std::equal(hs, hs + n, P.hs.begin())) continue;
+        bool same = true;
+        for (size_t j = 0; j < n && same; ++j) same = P.serials[j] == hs[j]->serial;
+        if (!same) continue;
+        if (k) std::rotate(g_copy_plans.begin(), g_copy_plans.begin() + k, g_copy_plans.begin() + k + 1);
+        *out = g_copy_plans[0].get();
+        return GOL_OK;
+    }
+    auto P = std::make_unique<CopyPlan>();
+    P->hs.assign(hs, hs + n);
     std::unordered_set<gol_handle> seen;
-    int64_t off = 0;
-    blocks = 0;
+    std::vector<CopyDesc> &d = P->d;
+    std::vector<int32_t> &bb = P->bb;
     d.resize(n);
     for (size_t i = 0; i < n; ++i) {
         gol_handle h = hs[i];
-        if (!valid(h)) return fail(GOL_EINVAL, "invalid handle at %zu", i);
-        if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board %zu is not packed", i);
-        if (scatter && !seen.insert(h).second) return fail(GOL_EINVAL, "handle repeated at %zu", i);
+        P->serials.push_back(h->serial);
+        if (!seen.insert(h).second) P->distinct = false;
         const int64_t nw = h->rows * h->words;
-        d[i].board = (uint64_t *)(scatter ? h->buf[0] : h->buf[h->cur]);
-        d[i].cur = scatter ? h->dev_cur : nullptr;
-        d[i].offset = off;
+        d[i].buf[0] = (uint64_t *)h->buf[0];
+        d[i].buf[1] = (uint64_t *)h->buf[1];
+        d[i].cur = h->dev_cur;
+        d[i].offset = P->nwords;
         d[i].nwords = nw;
         d[i].rows = h->rows;
         d[i].words = h->words;
         d[i].transposed = h->transposed;
         d[i].pad = 0;
-        d[i].block0 = blocks;
-        blocks += copy_blocks(d[i]);
-        off += nw;
+        d[i].block0 = P->blocks;
+        const int64_t nb = copy_blocks(d[i]);
+        if (P->blocks + nb > INT32_MAX) return fail(GOL_EINVAL, "too many words in one transfer");
+        bb.insert(bb.end(), (size_t)nb, (int32_t)i);
+        P->blocks += nb;
+        P->nwords += nw;
     }
-    if (blocks > INT32_MAX) return fail(GOL_EINVAL, "too many words in one transfer");
-    if ((size_t)off != nwords) return fail(GOL_EINVAL, "nwords = %zu, the boards hold %lld words", nwords, (long long)off);
+    P->board_off = (n * sizeof(CopyDesc) + 255) & ~size_t(255);
+    P->free_fn = g_free;
+    P->alloc_ctx = g_alloc_ctx;
+    P->dmem = dev_alloc(P->board_off + bb.size() * 4 + 4, g_alloc, g_alloc_ctx);
+    if (!P->dmem) return fail(GOL_ENOMEM, "transfer plan of %zu boards", n);
+    CU(cudaMemcpyAsync(P->dmem, d.data(), n * sizeof(CopyDesc), cudaMemcpyHostToDevice, g_stream));
+    CU(cudaMemcpyAsync((char *)P->dmem + P->board_off, bb.data(), bb.size() * 4, cudaMemcpyHostToDevice, g_stream));
+    g_copy_plans.insert(g_copy_plans.begin(), std::move(P));
+    if (g_copy_plans.size() > kMaxCopyPlans) g_copy_plans.pop_back();
+    *out = g_copy_plans[0].get();
     return GOL_OK;
+}
+}  // namespace
+
+namespace {
+// The device address of page-locked host memory registered with CUDA
+// (cudaHostAlloc, cudaHostRegister, a pinned torch tensor), which kernels on
+// this GPU read and write in place over the chip-to-chip link; null for any
+// other pointer (pageable memory goes through a staging buffer).
+const void *mapped_host_pointer(const void *p) {
+    if (!g_opt_zero_copy) return nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 }  // namespace
 
@@ -941,17 +1029,21 @@ int gol_set_packed_batch(const gol_handle *hs, size_t n, const uint64_t *words, 
     std::lock_guard<std::mutex> lk(g_mu);
     if (n == 0) return GOL_OK;
     if (!words) return fail(GOL_EINVAL, "null words");
-    std::vector<CopyDesc> d;
-    int64_t blocks = 0;
-    int rc = many_plan(hs, n, nwords, d, true, blocks);
+    const CopyPlan *P = nullptr;
+    int rc = copy_plan(hs, n, &P);
     if (rc) return rc;
-    const size_t dbytes = (n * sizeof(CopyDesc) + 255) & ~size_t(255);
-    Scratch st(dbytes + nwords * 8);
-    if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", nwords * 8);
-    CU(cudaMemcpyAsync(st.p, d.data(), n * sizeof(CopyDesc), cudaMemcpyHostToDevice, g_stream));
-    uint64_t *stage = (uint64_t *)((char *)st.p + dbytes);
-    CU(cudaMemcpyAsync(stage, words, nwords * 8, cudaMemcpyHostToDevice, g_stream));
-    CU(launch_scatter_boards((const CopyDesc *)st.p, (int)n, blocks, stage, g_stream));
+    if (!P->distinct) return fail(GOL_EINVAL, "a handle is repeated");
+    if ((int64_t)nwords != P->nwords)
+        return fail(GOL_EINVAL, "nwords = %zu, the boards hold %lld words", nwords, (long long)P->nwords);
+    const uint64_t *src = (const uint64_t *)mapped_host_pointer(words);
+    std::unique_ptr<Scratch> st;
+    if (!src) {
+        st.reset(new Scratch(nwords * 8));
+        if (!st->p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", nwords * 8);
+        CU(cudaMemcpyAsync(st->p, words, nwords * 8, cudaMemcpyHostToDevice, g_stream));
+        src = (const uint64_t *)st->p;
+    }
+    CU(launch_scatter_boards(P->desc(), P->block_board(), P->blocks, src, g_stream));
     for (size_t i = 0; i < n; ++i) {
         hs[i]->cur = 0;
         hs[i]->generation = 0;
@@ -963,17 +1055,19 @@ int gol_get_packed_batch(const gol_handle *hs, size_t n, uint64_t *words, size_t
     std::lock_guard<std::mutex> lk(g_mu);
     if (n == 0) return GOL_OK;
     if (!words) return fail(GOL_EINVAL, "null words");
-    std::vector<CopyDesc> d;
-    int64_t blocks = 0;
-    int rc = many_plan(hs, n, nwords, d, false, blocks);
+    const CopyPlan *P = nullptr;
+    int rc = copy_plan(hs, n, &P);
     if (rc) return rc;
-    const size_t dbytes = (n * sizeof(CopyDesc) + 255) & ~size_t(255);
-    Scratch st(dbytes + nwords * 8);
-    if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", nwords * 8);
-    CU(cudaMemcpyAsync(st.p, d.data(), n * sizeof(CopyDesc), cudaMemcpyHostToDevice, g_stream));
-    uint64_t *stage = (uint64_t *)((char *)st.p + dbytes);
-    CU(launch_gather_boards((const CopyDesc *)st.p, (int)n, blocks, stage, g_stream));
-    CU(cudaMemcpyAsync(words, stage, nwords * 8, cudaMemcpyDeviceToHost, g_stream));
+    if ((int64_t)nwords != P->nwords)
+        return fail(GOL_EINVAL, "nwords = %zu, the boards hold %lld words", nwords, (long long)P->nwords);
+    uint64_t *dst = (uint64_t *)mapped_host_pointer(words);
+    std::unique_ptr<Scratch> st;
+    if (!dst) {
+        st.reset(new Scratch(nwords * 8));
+        if (!st->p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", nwords * 8);
+    }
+    CU(launch_gather_boards(P->desc(), P->block_board(), P->blocks, dst ? dst : (uint64_t *)st->p, g_stream));
+    if (!dst) CU(cudaMemcpyAsync(words, st->p, nwords * 8, cudaMemcpyDeviceToHost, g_stream));
     return sync_stream();
 }
 
@@ -1147,6 +1241,14 @@ int gol_set_option(int key, int64_t v) {
             if (v < -1 || v > 2) return fail(GOL_EINVAL, "pipeline variant must be -1, 0, 1 or 2");
             g_opt_variant = v;
             return GOL_OK;
+        case GOL_OPT_ZERO_COPY:
+            if (v < 0 || v > 1) return fail(GOL_EINVAL, "zero copy must be 0 or 1");
+            g_opt_zero_copy = v;
+            return GOL_OK;
+        case GOL_OPT_BYTE_CLUSTER:
+            if (v < 0 || v > 1) return fail(GOL_EINVAL, "byte cluster must be 0 or 1");
+            g_opt_byte_cluster = v;
+            return GOL_OK;
     }
     return fail(GOL_EINVAL, "unknown option %d", key);
 }
@@ -1161,6 +1263,8 @@ int gol_get_option(int key, int64_t *v) {
         case GOL_OPT_ORIENTATION: *v = g_opt_orient; return GOL_OK;
         case GOL_OPT_CHAIN_PERMILLE: *v = g_opt_chain; return GOL_OK;
         case GOL_OPT_PIPELINE: *v = g_opt_variant; return GOL_OK;
+        case GOL_OPT_ZERO_COPY: *v = g_opt_zero_copy; return GOL_OK;
+        case GOL_OPT_BYTE_CLUSTER: *v = g_opt_byte_cluster; return GOL_OK;
     }
     return fail(GOL_EINVAL, "unknown option %d", key);
 }

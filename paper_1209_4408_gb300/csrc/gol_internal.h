@@ -124,8 +124,8 @@ __host__ __device__ __forceinline__ uint64_t to_interchange(uint64_t w) {
 __host__ __device__ __forceinline__ int resident_bit(int c) { return (c & 1) ? 32 + (c >> 1) : (c >> 1); }
 
 struct CopyDesc {
-    uint64_t *board;
-    int32_t *cur;       // scatter: reset to 0 (may be null)
+    uint64_t *buf[2];   // the board's buffers: scatter writes buf[0], gather reads buf[*cur]
+    int32_t *cur;       // the board's device `cur` (scatter resets it to 0)
     int64_t offset;
     int64_t nwords;
     int64_t rows;       // board geometry in the interchange layout
@@ -135,15 +135,17 @@ struct CopyDesc {
     int64_t block0;     // first block of this board in the copy grid
 };
 
-// Copy grid: a board takes ceil(words / kCopyWordsPerBlock) blocks, or
-// ceil(tiles / kCopyTilesPerBlock) when stored transposed (64 x 64 cell
-// tiles), at least one; the boards' blocks are consecutive.
+// Copy grid: a board takes ceil(words / kCopyWordsPerBlock) blocks, or, when
+// stored transposed, one block per super-tile of kSuper x kSuper tiles of
+// 64 x 64 cells; at least one; the boards' blocks are consecutive.
 constexpr int64_t kCopyWordsPerBlock = 4096;
-constexpr int64_t kCopyTilesPerBlock = 16;
+constexpr int kSuper = 8;
 __host__ __device__ __forceinline__ int64_t copy_blocks(const CopyDesc &c) {
-    const int64_t n = c.transposed ? (c.rows / 64) * c.words : c.nwords;
-    const int64_t per = c.transposed ? kCopyTilesPerBlock : kCopyWordsPerBlock;
-    return n > 0 ? (n + per - 1) / per : 1;
+    if (c.transposed) {
+        const int64_t n = ((c.rows / 64 + kSuper - 1) / kSuper) * ((c.words + kSuper - 1) / kSuper);
+        return n > 0 ? n : 1;
+    }
+    return c.nwords > 0 ? (c.nwords + kCopyWordsPerBlock - 1) / kCopyWordsPerBlock : 1;
 }
 
 // Launchers (one translation unit per K).  Return cudaGetLastError().
@@ -175,9 +177,18 @@ cudaError_t launch_popcount_packed(const uint64_t *words, int64_t n, unsigned lo
                                    cudaStream_t s);
 cudaError_t launch_popcount_bytes(const uint8_t *cells, int64_t n, unsigned long long *out,
                                   cudaStream_t s);
+// Byte boards in one thread-block cluster (kernels_util.cu): the cluster
+// size for an R x C board, 0 when a strip pair would not fit in shared memory.
+constexpr int kByteClusterMax = 8;                 // CTAs per cluster (portable size)
+constexpr int64_t kByteClusterBytes = 227 * 1024;  // shared memory per CTA
+int byte_cluster_size(int64_t R, int64_t C);
+cudaError_t launch_byte_cluster(const uint8_t *in, uint8_t *out, int64_t R, int64_t C, int torus, int G,
+                                cudaStream_t s);
 cudaError_t launch_convert(const uint64_t *src, uint64_t *dst, int64_t n, bool to_res, cudaStream_t s);
-cudaError_t launch_scatter_boards(const CopyDesc *d, int n, int64_t blocks, const uint64_t *staging, cudaStream_t s);
-cudaError_t launch_gather_boards(const CopyDesc *d, int n, int64_t blocks, uint64_t *staging, cudaStream_t s);
+cudaError_t launch_scatter_boards(const CopyDesc *d, const int32_t *block_board, int64_t blocks, const uint64_t *staging,
+                                  cudaStream_t s);
+cudaError_t launch_gather_boards(const CopyDesc *d, const int32_t *block_board, int64_t blocks, uint64_t *staging,
+                                 cudaStream_t s);
 cudaError_t launch_int_probe(unsigned *sink, int iters, int grid, int block, cudaStream_t s);
 int int_probe_ops_per_iter();   // 32-bit integer operations per thread per probe iteration
 

@@ -1,5 +1,7 @@
 // Byte-per-cell step, layout conversion, population count, scheduler
 // initialisation and the integer-throughput probe.
+#include <cooperative_groups.h>
+
 #include "gol_internal.h"
 #include "wavefront.cuh"
 
@@ -201,6 +203,59 @@ __global__ void popcount_kernel(const T *__restrict__ v, int64_t n, unsigned lon
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
+// --- byte-per-cell steps inside one thread-block cluster ------------------------
+// A board of at most kByteClusterBytes bytes per CTA strip runs G generations
+// in one launch of one cluster of n CTAs (n <= kByteClusterMax): CTA k owns
+// rows [R k / n, R (k + 1) / n), double-buffered in its shared memory (hmax =
+// ceil(R / n) rows per buffer).  The rows just above and below a strip are
+// read straight from the neighbouring CTAs' shared memory (distributed
+// shared memory, wrapping across the cluster on the torus, zero otherwise),
+// and a cluster barrier separates generations: after it every CTA's next
+// buffer is complete and nobody reads the previous one again.  Every strip
+// has at least one row (n <= R), so tiny tori alias exactly as the per-cell
+// kernel does (a strip's own rows stand in for missing neighbours).
+__global__ void byte_cluster_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int R, int C,
+                                    int torus, int G) {
+    extern __shared__ uint8_t sm[];
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int n = (int)cluster.num_blocks(), k = (int)cluster.block_rank();
+    const int hmax = (R + n - 1) / n;
+    const int r0 = (int)((int64_t)R * k / n), h = (int)((int64_t)R * (k + 1) / n) - r0;
+    const int up = (k + n - 1) % n, dn = (k + 1) % n;
+    const int h_up = (int)((int64_t)R * (up + 1) / n - (int64_t)R * up / n);
+    const bool has_up = torus || k > 0, has_dn = torus || k < n - 1;
+    for (int i = threadIdx.x; i < h * C; i += blockDim.x) sm[i] = in[(int64_t)r0 * C + i] != 0;
+    cluster.sync();
+    for (int g = 0; g < G; ++g) {
+        const int cb = g & 1;
+        const uint8_t *cur = sm + (size_t)cb * hmax * C;
+        uint8_t *nxt = sm + (size_t)(cb ^ 1) * hmax * C;
+        // the neighbours' current buffers (row above this strip: the last row of `up`)
+        const uint8_t *above = cluster.map_shared_rank(sm, up) + (size_t)cb * hmax * C + (size_t)(h_up - 1) * C;
+        const uint8_t *below = cluster.map_shared_rank(sm, dn) + (size_t)cb * hmax * C;
+        for (int i = threadIdx.x; i < h * C; i += blockDim.x) {
+            const int lr = i / C, c = i - lr * C;
+            const uint8_t *rows[3] = {lr > 0 ? cur + (size_t)(lr - 1) * C : (has_up ? above : nullptr), cur + (size_t)lr * C,
+                                      lr < h - 1 ? cur + (size_t)(lr + 1) * C : (has_dn ? below : nullptr)};
+            const int cl = c > 0 ? c - 1 : (torus ? C - 1 : -1), cr = c < C - 1 ? c + 1 : (torus ? 0 : -1);
+            int cnt = 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const uint8_t *row = rows[d];
+                if (!row) continue;
+                if (cl >= 0) cnt += row[cl];
+                if (d != 1) cnt += row[c];
+                if (cr >= 0) cnt += row[cr];
+            }
+            nxt[i] = (cnt == 3) || (cur[i] && cnt == 2);
+        }
+        cluster.sync();
+    }
+    const uint8_t *res = sm + (size_t)(G & 1) * hmax * C;
+    for (int i = threadIdx.x; i < h * C; i += blockDim.x) out[(int64_t)r0 * C + i] = res[i];
+}
+
 // --- interchange <-> resident word layout ---------------------------------------
 __global__ void convert_kernel(const uint64_t *src, uint64_t *dst, int64_t n, bool to_res) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -242,6 +297,66 @@ __device__ __forceinline__ void transpose_tile(const uint64_t *__restrict__ src,
     dst[(64 * tj + 32 + lane) * dst_w + ti] = out_b;
 }
 
+// One block of 256 threads (8 warps) moves a super-tile of kSuper x kSuper
+// such tiles with full 64-byte rows on both sides.  src holds src_rows x
+// src_w words (src_rows % 64 == 0); dst is its transpose, (64 src_w) x
+// (src_rows / 64) words.  Super-tile (si, sj) covers tile rows
+// ti in [8 si, 8 si + 8) and tile columns tj in [8 sj, 8 sj + 8): warp w
+// reads rows 64 (8 si + w) + lane and + 32, words 8 sj .. 8 sj + 7 of each,
+// transposes its tiles with ballots into shared memory, and the block then
+// writes output rows 64 tj + r, words 8 si .. 8 si + 7.  Tiles past the
+// edges of the board are skipped.  Every thread of the block must call it.
+__device__ void transpose_super(const uint64_t *__restrict__ src, int64_t src_rows, int64_t src_w,
+                                uint64_t *__restrict__ dst, int64_t si, int64_t sj, bool from_res, bool to_res) {
+    __shared__ uint64_t sm[kSuper][64][kSuper + 1];   // [tile column][row][tile row], padded
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nti = src_rows / 64;
+    const int nk = (int)min((int64_t)kSuper, src_w - kSuper * sj);   // tile columns present
+    const int nw = (int)min((int64_t)kSuper, nti - kSuper * si);     // tile rows present
+    if (w < nw) {
+        const uint64_t *ra = src + (64 * (kSuper * si + w) + lane) * src_w + kSuper * sj;
+        const uint64_t *rb = ra + 32 * src_w;
+        uint64_t a[kSuper], b[kSuper];
+#pragma unroll
+        for (int k = 0; k < kSuper; ++k) {
+            a[k] = k < nk ? ra[k] : 0;
+            b[k] = k < nk ? rb[k] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kSuper; ++k) {
+            if (k >= nk) break;
+            const uint64_t x = from_res ? to_interchange(a[k]) : a[k];
+            const uint64_t y = from_res ? to_interchange(b[k]) : b[k];
+            uint64_t out_a = 0, out_b = 0;   // output rows 64 tj + lane and 64 tj + 32 + lane
+#pragma unroll 8
+            for (int j = 0; j < 64; ++j) {
+                const uint32_t lo = __ballot_sync(0xffffffffu, (uint32_t)(x >> j) & 1u);
+                const uint32_t hi = __ballot_sync(0xffffffffu, (uint32_t)(y >> j) & 1u);
+                const uint64_t v = (uint64_t)lo | ((uint64_t)hi << 32);
+                if (j == lane) out_a = v;
+                if (j == lane + 32) out_b = v;
+            }
+            sm[k][lane][w] = to_res ? to_resident(out_a) : out_a;
+            sm[k][lane + 32][w] = to_res ? to_resident(out_b) : out_b;
+        }
+    }
+    __syncthreads();
+    const int64_t dst_w = nti;
+    for (int idx = threadIdx.x; idx < kSuper * 64 * kSuper; idx += blockDim.x) {
+        const int ww = idx % kSuper, r = (idx / kSuper) % 64, k = idx / (64 * kSuper);
+        if (ww < nw && k < nk) dst[(64 * (kSuper * sj + k) + r) * dst_w + kSuper * si + ww] = sm[k][r][ww];
+    }
+}
+
+// Transposed orientation, super-tile per block: the board (R rows, W words)
+// to its stored transpose (to_res), or back.
+__global__ void orient_super_kernel(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, int64_t R,
+                                    int64_t W, bool to_res) {
+    const int64_t src_rows = to_res ? R : 64 * W, src_w = to_res ? W : R / 64;
+    const int64_t nsj = (src_w + kSuper - 1) / kSuper;
+    transpose_super(src, src_rows, src_w, dst, blockIdx.x / nsj, blockIdx.x % nsj, !to_res, to_res);
+}
+
 // R x W interchange words -> resident storage: (64 W) x (R / 64) when
 // transposed, else R x W.  Reverse direction with to_res = false.
 __global__ void orient_kernel(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, int64_t R, int64_t W,
@@ -265,46 +380,38 @@ __global__ void orient_kernel(const uint64_t *__restrict__ src, uint64_t *__rest
 }
 
 // --- many boards <-> one contiguous staging buffer ----------------------------
-// The copy grid holds copy_blocks(d[i]) consecutive blocks per board; a block
-// finds its board by binary search on block0 and copies its share of the
-// board's words (or 64 x 64 tiles when the board is stored transposed).
-__device__ __forceinline__ int copy_board_of_block(const CopyDesc *__restrict__ d, int n, int64_t b) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (d[mid].block0 <= b) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// a null `cur` is not written
-__global__ void scatter_boards_kernel(const CopyDesc *__restrict__ d, int n, const uint64_t *__restrict__ staging) {
-    const CopyDesc c = d[copy_board_of_block(d, n, blockIdx.x)];
+// The copy grid holds copy_blocks(d[i]) consecutive blocks per board;
+// block_board maps a block to its board.  A block copies its share of the
+// board's words, or one super-tile when the board is stored transposed.
+__global__ void scatter_boards_kernel(const CopyDesc *__restrict__ d, const int32_t *__restrict__ block_board,
+                                      const uint64_t *__restrict__ staging) {
+    const CopyDesc c = d[block_board[blockIdx.x]];
     const int64_t lb = blockIdx.x - c.block0;
     if (!c.transposed) {
         const int64_t end = min(c.nwords, (lb + 1) * kCopyWordsPerBlock);
         for (int64_t i = lb * kCopyWordsPerBlock + threadIdx.x; i < end; i += blockDim.x)
-            c.board[i] = to_resident(staging[c.offset + i]);
+            c.buf[0][i] = to_resident(staging[c.offset + i]);
     } else {
-        const int64_t end = min((c.rows / 64) * c.words, (lb + 1) * kCopyTilesPerBlock);
-        for (int64_t t = lb * kCopyTilesPerBlock + threadIdx.x / 32; t < end; t += blockDim.x / 32)
-            transpose_tile(staging + c.offset, c.words, t / c.words, t % c.words, c.board, c.rows / 64, false, true);
+        // super-tile lb of the board (rows x words interchange) -> its stored transpose
+        const int64_t nsj = (c.words + kSuper - 1) / kSuper;
+        transpose_super(staging + c.offset, c.rows, c.words, c.buf[0], lb / nsj, lb % nsj, false, true);
     }
-    if (lb == 0 && threadIdx.x == 0 && c.cur) *c.cur = 0;
+    if (lb == 0 && threadIdx.x == 0) *c.cur = 0;
 }
 
-__global__ void gather_boards_kernel(const CopyDesc *__restrict__ d, int n, uint64_t *__restrict__ staging) {
-    const CopyDesc c = d[copy_board_of_block(d, n, blockIdx.x)];
+__global__ void gather_boards_kernel(const CopyDesc *__restrict__ d, const int32_t *__restrict__ block_board,
+                                     uint64_t *__restrict__ staging) {
+    const CopyDesc c = d[block_board[blockIdx.x]];
     const int64_t lb = blockIdx.x - c.block0;
+    const uint64_t *board = c.buf[*c.cur & 1];
     if (!c.transposed) {
         const int64_t end = min(c.nwords, (lb + 1) * kCopyWordsPerBlock);
         for (int64_t i = lb * kCopyWordsPerBlock + threadIdx.x; i < end; i += blockDim.x)
-            staging[c.offset + i] = to_interchange(c.board[i]);
+            staging[c.offset + i] = to_interchange(board[i]);
     } else {
-        const int64_t rb = c.rows / 64;
-        const int64_t end = min(rb * c.words, (lb + 1) * kCopyTilesPerBlock);
-        for (int64_t t = lb * kCopyTilesPerBlock + threadIdx.x / 32; t < end; t += blockDim.x / 32)
-            transpose_tile(c.board, rb, t / rb, t % rb, staging + c.offset, c.words, true, false);
+        // super-tile lb of the stored transpose (64 words x rows / 64) -> interchange rows
+        const int64_t rb = c.rows / 64, nsj = (rb + kSuper - 1) / kSuper;
+        transpose_super(board, 64 * c.words, rb, staging + c.offset, lb / nsj, lb % nsj, true, false);
     }
 }
 
@@ -378,8 +485,12 @@ cudaError_t launch_region_packed(const uint64_t *words, int64_t R, int64_t W, in
 cudaError_t launch_orient(const uint64_t *src, uint64_t *dst, int64_t R, int64_t W, bool transposed, bool to_res,
                           cudaStream_t s) {
     if (R * W == 0) return cudaSuccess;
-    const int64_t work = transposed ? (R / 64) * W * 32 : R * W;   // threads
-    orient_kernel<<<grid_for(work, kBlock, 1 << 16), kBlock, 0, s>>>(src, dst, R, W, transposed, to_res);
+    if (transposed) {
+        const int64_t nsuper = ((R / 64 + kSuper - 1) / kSuper) * ((W + kSuper - 1) / kSuper);
+        orient_super_kernel<<<(unsigned)nsuper, kBlock, 0, s>>>(src, dst, R, W, to_res);
+    } else {
+        orient_kernel<<<grid_for(R * W, kBlock, 1 << 16), kBlock, 0, s>>>(src, dst, R, W, false, to_res);
+    }
     return cudaGetLastError();
 }
 
@@ -406,15 +517,46 @@ cudaError_t launch_convert(const uint64_t *src, uint64_t *dst, int64_t n, bool t
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_boards(const CopyDesc *d, int n, int64_t blocks, const uint64_t *staging,
+cudaError_t launch_scatter_boards(const CopyDesc *d, const int32_t *block_board, int64_t blocks, const uint64_t *staging,
                                   cudaStream_t s) {
-    if (n > 0 && blocks > 0) scatter_boards_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(d, n, staging);
+    if (blocks > 0) scatter_boards_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(d, block_board, staging);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_boards(const CopyDesc *d, int n, int64_t blocks, uint64_t *staging, cudaStream_t s) {
-    if (n > 0 && blocks > 0) gather_boards_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(d, n, staging);
+cudaError_t launch_gather_boards(const CopyDesc *d, const int32_t *block_board, int64_t blocks, uint64_t *staging,
+                                 cudaStream_t s) {
+    if (blocks > 0) gather_boards_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(d, block_board, staging);
     return cudaGetLastError();
+}
+
+int byte_cluster_size(int64_t R, int64_t C) {
+    if (R < 1 || C < 1 || R > (1 << 20) || C > (1 << 20)) return 0;
+    const int n = (int)std::min<int64_t>(kByteClusterMax, R);
+    const int64_t hmax = (R + n - 1) / n;
+    return 2 * hmax * C <= kByteClusterBytes ? n : 0;
+}
+
+cudaError_t launch_byte_cluster(const uint8_t *in, uint8_t *out, int64_t R, int64_t C, int torus, int G,
+                                cudaStream_t s) {
+    const int n = byte_cluster_size(R, C);
+    if (n == 0 || G < 1) return cudaErrorInvalidValue;
+    const int64_t hmax = (R + n - 1) / n;
+    const size_t smem = (size_t)(2 * hmax * C);
+    cudaError_t e = cudaFuncSetAttribute(byte_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n, 1, 1);
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)n;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, byte_cluster_kernel, in, out, (int)R, (int)C, torus, G);
 }
 
 cudaError_t launch_int_probe(unsigned *sink, int iters, int grid, int block, cudaStream_t s) {

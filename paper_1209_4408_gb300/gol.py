@@ -40,6 +40,8 @@ GOL_OPT_WAIT_TIMEOUT_MS = 4
 GOL_OPT_ORIENTATION = 5
 GOL_OPT_CHAIN_PERMILLE = 6
 GOL_OPT_PIPELINE = 7
+GOL_OPT_ZERO_COPY = 8
+GOL_OPT_BYTE_CLUSTER = 9
 
 # every symbol declared in include/gol.h
 EXPORTED = (
@@ -190,7 +192,9 @@ def gol_get_packed_device(h: int, dptr: int, nwords: int):
 
 
 def _handles(hs) -> np.ndarray:
-    return np.ascontiguousarray(np.array(list(hs), dtype=np.uint64))
+    if isinstance(hs, np.ndarray):
+        return np.ascontiguousarray(hs, dtype=np.uint64)
+    return np.array(hs, dtype=np.uint64)
 
 
 def gol_set_packed_batch(hs: Sequence[int], words: np.ndarray):
@@ -219,8 +223,9 @@ def gol_step(h: int, generations: int):
 
 
 def gol_step_batch(hs: Sequence[int], generations: Iterable[int]):
-    hs_a = np.ascontiguousarray(np.array(list(hs), dtype=np.uint64))
-    g_a = np.ascontiguousarray(np.array(list(generations), dtype=np.int64))
+    hs_a = _handles(hs)
+    g_a = (np.ascontiguousarray(generations, dtype=np.int64) if isinstance(generations, np.ndarray)
+           else np.array(list(generations), dtype=np.int64))
     if hs_a.size != g_a.size:
         raise ValueError("handles and generation counts differ in length")
     _check(load().gol_step_batch(_ptr(hs_a), _ptr(g_a), hs_a.size))

@@ -344,6 +344,49 @@ def test_many_board_transfers(gol):
 
 
 @pytest.mark.parametrize("orient", [1, 2])
+@pytest.mark.parametrize("zero_copy", [1, 0])
+def test_many_board_transfers_pinned_and_pageable(gol, orient, zero_copy):
+    # batch transfers through pinned host memory (read and written in place
+    # unless zero copy is off) and through pageable memory (staged), on
+    # boards whose 8 x 8-tile blocks are ragged in both directions
+    import torch
+
+    shapes = [(576, 704), (640, 1216), (128, 2176), (1088, 512), (64, 64), (192, 4032)]
+    gol.gol_set_option(gol.GOL_OPT_ORIENTATION, orient)
+    gol.gol_set_option(gol.GOL_OPT_ZERO_COPY, zero_copy)
+    try:
+        cells = [synth.bernoulli_board(R, C, 0.4, 1300 + i) for i, (R, C) in enumerate(shapes)]
+        flat = np.concatenate([synth.pack_cells(c).reshape(-1) for c in cells])
+        n = flat.size
+        # a pinned buffer with the boards at an offset inside the allocation
+        pin = torch.empty(n + 5, dtype=torch.int64, pin_memory=True)
+        pinned = pin.numpy().view(np.uint64)[3:3 + n]
+        for host_in in (pinned, flat.copy()):
+            host_in[:] = flat
+            boards = [gol.Board(R, C) for R, C in shapes]
+            hs = [b.handle for b in boards]
+            gol.gol_set_packed_batch(hs, host_in)
+            out = np.zeros_like(flat)
+            gol.gol_get_packed_batch(hs, out)
+            np.testing.assert_array_equal(out, flat)
+            gol.step_batch(boards, [9] * len(boards))
+            pin_out = torch.zeros(n + 1, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)[1:]
+            for host_out in (pin_out, np.zeros_like(flat)):
+                gol.gol_get_packed_batch(hs, host_out)
+                off = 0
+                for (R, C), c in zip(shapes, cells):
+                    k = R * C // 64
+                    assert_same(oracle.unpack_words(host_out[off:off + k].reshape(R, C // 64)), oracle.run(c, 9),
+                                "%dx%d orient %d zero copy %d" % (R, C, orient, zero_copy))
+                    off += k
+            for b in boards:
+                b.close()
+    finally:
+        gol.gol_set_option(gol.GOL_OPT_ORIENTATION, 0)
+        gol.gol_set_option(gol.GOL_OPT_ZERO_COPY, 1)
+
+
+@pytest.mark.parametrize("orient", [1, 2])
 def test_storage_orientation_all_io_paths(gol, orient):
     # the same results whether the library stores the board as is (1) or
     # transposed (2), through every way in and out of the device
