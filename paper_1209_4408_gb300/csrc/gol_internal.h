@@ -177,8 +177,9 @@ cudaError_t launch_popcount_packed(const uint64_t *words, int64_t n, unsigned lo
                                    cudaStream_t s);
 cudaError_t launch_popcount_bytes(const uint8_t *cells, int64_t n, unsigned long long *out,
                                   cudaStream_t s);
-// Byte boards in one thread-block cluster (kernels_util.cu): the cluster
-// size for an R x C board, 0 when a strip pair would not fit in shared memory.
+// Byte boards resident, one bit per cell, in one thread-block cluster
+// (kernels_util.cu): the cluster size for an R x C board (the smallest power
+// of two whose CTAs hold two buffers of their strip), 0 when none does.
 constexpr int kByteClusterMax = 8;                 // CTAs per cluster (portable size)
 constexpr int64_t kByteClusterBytes = 227 * 1024;  // shared memory per CTA
 int byte_cluster_size(int64_t R, int64_t C);

@@ -203,57 +203,108 @@ __global__ void popcount_kernel(const T *__restrict__ v, int64_t n, unsigned lon
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
-// --- byte-per-cell steps inside one thread-block cluster ------------------------
-// A board of at most kByteClusterBytes bytes per CTA strip runs G generations
-// in one launch of one cluster of n CTAs (n <= kByteClusterMax): CTA k owns
-// rows [R k / n, R (k + 1) / n), double-buffered in its shared memory (hmax =
-// ceil(R / n) rows per buffer).  The rows just above and below a strip are
-// read straight from the neighbouring CTAs' shared memory (distributed
-// shared memory, wrapping across the cluster on the torus, zero otherwise),
-// and a cluster barrier separates generations: after it every CTA's next
-// buffer is complete and nobody reads the previous one again.  Every strip
-// has at least one row (n <= R), so tiny tori alias exactly as the per-cell
-// kernel does (a strip's own rows stand in for missing neighbours).
-__global__ void byte_cluster_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int R, int C,
-                                    int torus, int G) {
-    extern __shared__ uint8_t sm[];
+// --- byte-per-cell boards resident in one thread-block cluster -----------------
+// A byte board whose cells fit, one bit each, in the shared memory of a
+// cluster of n <= kByteClusterMax CTAs runs G generations in one launch.
+// CTA k packs rows [R k / n, R (k + 1) / n) into words (bit j of word w =
+// column 64 w + j, W = ceil(C / 64) words per row, the last one holding
+// C - 64 (W - 1) columns), double-buffered, steps them with the same
+// bit-sliced rule as the packed boards, and unpacks the result.  The rows just
+// above and below a strip are read from the neighbouring CTAs' shared memory
+// (distributed shared memory; wrapping across the cluster on the torus, zero
+// otherwise) and a cluster barrier separates generations.  Every strip has at
+// least one row (n <= R), and the horizontal wrap takes column C - 1 / 0 from
+// wherever it sits, so tiny tori alias exactly as the per-cell kernel does.
+__device__ __forceinline__ uint64_t byte_rule(uint64_t t0, uint64_t t1, uint64_t m0, uint64_t m1, uint64_t b0,
+                                              uint64_t b1, uint64_t a) {
+    // S = (t0 + m0 + b0) + 2 (t1 + m1 + b1) = u0 + 2 (u1 + p) + 4 q; next = S==3 | (a & S==4)
+    const uint64_t u0 = t0 ^ m0 ^ b0, u1 = (t0 & m0) | (b0 & (t0 ^ m0));
+    const uint64_t p = t1 ^ m1 ^ b1, q = (t1 & m1) | (b1 & (t1 ^ m1));
+    const uint64_t e = p ^ u1;
+    return (u0 & e & ~q) | (~u0 & ~e & (p ^ q) & a);
+}
+
+// Row-sum planes (s0 + 2 s1 = west + cell + east) of word w of a row.
+__device__ __forceinline__ void byte_row_sum(const uint64_t *row, int w, int W, int last_bits, bool torus,
+                                             uint64_t &s0, uint64_t &s1) {
+    const uint64_t x = row[w];
+    uint64_t wc, ec;   // west neighbour of bit 0, east neighbour of the top valid bit
+    if (w > 0) wc = row[w - 1] >> 63;
+    else wc = torus ? (row[W - 1] >> (last_bits - 1)) & 1 : 0;
+    if (w < W - 1) ec = row[w + 1] & 1;
+    else ec = torus ? row[0] & 1 : 0;
+    const uint64_t west = (x << 1) | wc;
+    const uint64_t east = w < W - 1 ? (x >> 1) | (ec << 63) : (x >> 1) | (ec << (last_bits - 1));
+    s0 = west ^ x ^ east;
+    s1 = (west & x) | (east & (west ^ x));
+}
+
+// CLUSTERED: n > 1 CTAs exchanging halo rows through distributed shared
+// memory; otherwise one CTA whose strip is the whole board.
+template <bool CLUSTERED>
+__global__ void byte_resident_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int R, int C,
+                                     int torus, int G) {
+    extern __shared__ uint64_t smw[];
     namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int n = (int)cluster.num_blocks(), k = (int)cluster.block_rank();
+    const int n = CLUSTERED ? (int)cg::this_cluster().num_blocks() : 1;
+    const int k = CLUSTERED ? (int)cg::this_cluster().block_rank() : 0;
+    const int W = (C + 63) / 64, last_bits = C - 64 * (W - 1);
+    const uint64_t last_mask = last_bits == 64 ? ~0ull : (1ull << last_bits) - 1;
     const int hmax = (R + n - 1) / n;
     const int r0 = (int)((int64_t)R * k / n), h = (int)((int64_t)R * (k + 1) / n) - r0;
     const int up = (k + n - 1) % n, dn = (k + 1) % n;
     const int h_up = (int)((int64_t)R * (up + 1) / n - (int64_t)R * up / n);
     const bool has_up = torus || k > 0, has_dn = torus || k < n - 1;
-    for (int i = threadIdx.x; i < h * C; i += blockDim.x) sm[i] = in[(int64_t)r0 * C + i] != 0;
-    cluster.sync();
+    const size_t buf_words = (size_t)hmax * W;
+    const int nw = h * W;
+    // this thread's first word (row lr0, word w0) and the stride in rows / words
+    const int lr0 = (int)threadIdx.x / W, w0 = (int)threadIdx.x - lr0 * W;
+    const int step_r = (int)blockDim.x / W, step_w = (int)blockDim.x - step_r * W;
+    for (int i = threadIdx.x, lr = lr0, w = w0; i < nw; i += blockDim.x) {
+        const uint8_t *src = in + (int64_t)(r0 + lr) * C + 64 * w;
+        const int nb = w < W - 1 ? 64 : last_bits;
+        uint64_t v = 0;
+        for (int j = 0; j < nb; ++j) v |= (uint64_t)(src[j] != 0) << j;
+        smw[i] = v;
+        lr += step_r;
+        w += step_w;
+        if (w >= W) { w -= W; ++lr; }
+    }
+    if (CLUSTERED) cg::this_cluster().sync(); else __syncthreads();
     for (int g = 0; g < G; ++g) {
         const int cb = g & 1;
-        const uint8_t *cur = sm + (size_t)cb * hmax * C;
-        uint8_t *nxt = sm + (size_t)(cb ^ 1) * hmax * C;
-        // the neighbours' current buffers (row above this strip: the last row of `up`)
-        const uint8_t *above = cluster.map_shared_rank(sm, up) + (size_t)cb * hmax * C + (size_t)(h_up - 1) * C;
-        const uint8_t *below = cluster.map_shared_rank(sm, dn) + (size_t)cb * hmax * C;
-        for (int i = threadIdx.x; i < h * C; i += blockDim.x) {
-            const int lr = i / C, c = i - lr * C;
-            const uint8_t *rows[3] = {lr > 0 ? cur + (size_t)(lr - 1) * C : (has_up ? above : nullptr), cur + (size_t)lr * C,
-                                      lr < h - 1 ? cur + (size_t)(lr + 1) * C : (has_dn ? below : nullptr)};
-            const int cl = c > 0 ? c - 1 : (torus ? C - 1 : -1), cr = c < C - 1 ? c + 1 : (torus ? 0 : -1);
-            int cnt = 0;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const uint8_t *row = rows[d];
-                if (!row) continue;
-                if (cl >= 0) cnt += row[cl];
-                if (d != 1) cnt += row[c];
-                if (cr >= 0) cnt += row[cr];
-            }
-            nxt[i] = (cnt == 3) || (cur[i] && cnt == 2);
+        const uint64_t *cur = smw + cb * buf_words;
+        uint64_t *nxt = smw + (cb ^ 1) * buf_words;
+        const uint64_t *above, *below;
+        if (CLUSTERED) {
+            above = cg::this_cluster().map_shared_rank(smw, up) + cb * buf_words + (size_t)(h_up - 1) * W;
+            below = cg::this_cluster().map_shared_rank(smw, dn) + cb * buf_words;
+        } else {
+            above = cur + (size_t)(h - 1) * W;     // the torus wraps within the board
+            below = cur;
         }
-        cluster.sync();
+        for (int i = threadIdx.x, lr = lr0, w = w0; i < nw; i += blockDim.x) {
+            const uint64_t *rm = cur + (size_t)lr * W;
+            const uint64_t *ra = lr > 0 ? rm - W : (has_up ? above : nullptr);
+            const uint64_t *rb = lr < h - 1 ? rm + W : (has_dn ? below : nullptr);
+            uint64_t t0 = 0, t1 = 0, m0, m1, b0 = 0, b1 = 0;
+            if (ra) byte_row_sum(ra, w, W, last_bits, torus, t0, t1);
+            byte_row_sum(rm, w, W, last_bits, torus, m0, m1);
+            if (rb) byte_row_sum(rb, w, W, last_bits, torus, b0, b1);
+            uint64_t v = byte_rule(t0, t1, m0, m1, b0, b1, rm[w]);
+            if (w == W - 1) v &= last_mask;
+            nxt[i] = v;
+            lr += step_r;
+            w += step_w;
+            if (w >= W) { w -= W; ++lr; }
+        }
+        if (CLUSTERED) cg::this_cluster().sync(); else __syncthreads();
     }
-    const uint8_t *res = sm + (size_t)(G & 1) * hmax * C;
-    for (int i = threadIdx.x; i < h * C; i += blockDim.x) out[(int64_t)r0 * C + i] = res[i];
+    const uint64_t *res = smw + (G & 1) * buf_words;
+    for (int i = threadIdx.x; i < h * C; i += blockDim.x) {
+        const int lr = i / C, c = i - lr * C;
+        out[(int64_t)(r0 + lr) * C + c] = (uint8_t)((res[(size_t)lr * W + (c >> 6)] >> (c & 63)) & 1);
+    }
 }
 
 // --- interchange <-> resident word layout ---------------------------------------
@@ -531,18 +582,29 @@ cudaError_t launch_gather_boards(const CopyDesc *d, const int32_t *block_board, 
 
 int byte_cluster_size(int64_t R, int64_t C) {
     if (R < 1 || C < 1 || R > (1 << 20) || C > (1 << 20)) return 0;
-    const int n = (int)std::min<int64_t>(kByteClusterMax, R);
-    const int64_t hmax = (R + n - 1) / n;
-    return 2 * hmax * C <= kByteClusterBytes ? n : 0;
+    const int64_t W = (C + 63) / 64;
+    for (int n = 1; n <= kByteClusterMax && n <= R; n *= 2) {
+        const int64_t hmax = (R + n - 1) / n;
+        if (2 * hmax * W * 8 <= kByteClusterBytes) return n;
+    }
+    return 0;
 }
 
 cudaError_t launch_byte_cluster(const uint8_t *in, uint8_t *out, int64_t R, int64_t C, int torus, int G,
                                 cudaStream_t s) {
     const int n = byte_cluster_size(R, C);
     if (n == 0 || G < 1) return cudaErrorInvalidValue;
-    const int64_t hmax = (R + n - 1) / n;
-    const size_t smem = (size_t)(2 * hmax * C);
-    cudaError_t e = cudaFuncSetAttribute(byte_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t hmax = (R + n - 1) / n, W = (C + 63) / 64;
+    const size_t smem = (size_t)(2 * hmax * W * 8);
+    if (n == 1) {
+        cudaError_t e = cudaFuncSetAttribute(byte_resident_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        byte_resident_kernel<false><<<1, 1024, smem, s>>>(in, out, (int)R, (int)C, torus, G);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaFuncSetAttribute(byte_resident_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)n, 1, 1);
@@ -556,7 +618,7 @@ cudaError_t launch_byte_cluster(const uint8_t *in, uint8_t *out, int64_t R, int6
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, byte_cluster_kernel, in, out, (int)R, (int)C, torus, G);
+    return cudaLaunchKernelEx(&cfg, byte_resident_kernel<true>, in, out, (int)R, (int)C, torus, G);
 }
 
 cudaError_t launch_int_probe(unsigned *sink, int iters, int grid, int block, cudaStream_t s) {

@@ -87,6 +87,32 @@ def test_bytes_random_multi_gen(gol, R, C):
                     "bytes %dx%d" % (R, C))
 
 
+@pytest.mark.parametrize("cluster", [1, 0])
+@pytest.mark.parametrize("R,C", [(1, 1), (2, 3), (9, 1), (7, 9), (16, 16), (33, 65), (100, 700), (960, 960),
+                                 (1000, 1600), (1500, 1500), (2048, 2048), (3072, 3072)])
+def test_bytes_cluster_and_per_generation_paths(gol, cluster, R, C):
+    # boards whose cells fit, one bit each, in a cluster's shared memory
+    # (two buffers of ceil(R / n) rows of ceil(C / 64) words per CTA, n <= 8:
+    # 2048 x 2048 does) run all generations in one cluster launch; 3072 x
+    # 3072 and option 0 take one launch per generation; both match the
+    # oracle, torus and bounded
+    gol.gol_set_option(gol.GOL_OPT_BYTE_CLUSTER, cluster)
+    try:
+        cells = synth.bernoulli_board(R, C, 0.35, 7 * R + C)
+        for torus in (True, False):
+            b = gol.Board(R, C, torus=torus, layout=gol.GOL_LAYOUT_BYTES)
+            b.set(cells)
+            x = cells
+            for g in (1, 2, 13):
+                b.step(g)
+                x = oracle.run(x, g, torus)
+                assert_same(b.get(), x, "bytes %dx%d torus=%s cluster=%d" % (R, C, torus, cluster))
+            assert b.generation() == 16
+            b.close()
+    finally:
+        gol.gol_set_option(gol.GOL_OPT_BYTE_CLUSTER, 1)
+
+
 # ---------------------------------------------------------------------------
 # packed path: the rule at every bit position and across both wraps
 # ---------------------------------------------------------------------------
@@ -470,6 +496,7 @@ def test_bytes_graph_replay_on_torch_stream(gol):
 
     stream = torch.cuda.Stream()
     gol.gol_set_stream(stream)
+    gol.gol_set_option(gol.GOL_OPT_BYTE_CLUSTER, 0)    # the per-generation launches
     try:
         cells = synth.bernoulli_board(100, 130, 0.35, 2)
         b = gol.Board(100, 130, layout=gol.GOL_LAYOUT_BYTES)
@@ -481,4 +508,5 @@ def test_bytes_graph_replay_on_torch_stream(gol):
         assert b.generation() == 430
         b.close()
     finally:
+        gol.gol_set_option(gol.GOL_OPT_BYTE_CLUSTER, 1)
         gol.gol_set_stream(None)
