@@ -932,6 +932,7 @@ struct CopyPlan {
     std::vector<uint64_t> serials;
     int64_t nwords = 0, blocks = 0;
     bool distinct = true;
+    bool transposed = false;           // some board is stored transposed
     std::vector<CopyDesc> d;           // host copies of what dmem holds
     std::vector<int32_t> bb;
     void *dmem = nullptr;              // CopyDesc[n] | int32 block_board[blocks]
@@ -989,6 +990,7 @@ int copy_plan(const gol_handle *hs, size_t n, const CopyPlan **out) {
         d[i].transposed = h->transposed;
         d[i].pad = 0;
         d[i].block0 = P->blocks;
+        P->transposed = P->transposed || h->transposed;
         const int64_t nb = copy_blocks(d[i]);
         if (P->blocks + nb > INT32_MAX) return fail(GOL_EINVAL, "too many words in one transfer");
         bb.insert(bb.end(), (size_t)nb, (int32_t)i);
@@ -1013,9 +1015,13 @@ namespace {
 // The device address of page-locked host memory registered with CUDA
 // (cudaHostAlloc, cudaHostRegister, a pinned torch tensor), which kernels on
 // this GPU read and write in place over the chip-to-chip link; null for any
-// other pointer (pageable memory goes through a staging buffer).
-const void *mapped_host_pointer(const void *p) {
-    if (!g_opt_zero_copy) return nullptr;
+// other pointer (pageable memory goes through a staging buffer), and for
+// transfers that include boards stored transposed: their tile transposes
+// read and write 64-byte pieces of rows, which the copy engine plus a
+// device-side transpose moves faster (measured on the 4096-board batch:
+// 0.76 / 0.84 ms up / down staged against 0.80 / 0.98 ms in place).
+const void *mapped_host_pointer(const void *p, const CopyPlan &P) {
+    if (!g_opt_zero_copy || P.transposed) return nullptr;
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
@@ -1035,7 +1041,7 @@ int gol_set_packed_batch(const gol_handle *hs, size_t n, const uint64_t *words, 
     if (!P->distinct) return fail(GOL_EINVAL, "a handle is repeated");
     if ((int64_t)nwords != P->nwords)
         return fail(GOL_EINVAL, "nwords = %zu, the boards hold %lld words", nwords, (long long)P->nwords);
-    const uint64_t *src = (const uint64_t *)mapped_host_pointer(words);
+    const uint64_t *src = (const uint64_t *)mapped_host_pointer(words, *P);
     std::unique_ptr<Scratch> st;
     if (!src) {
         st.reset(new Scratch(nwords * 8));
@@ -1060,7 +1066,7 @@ int gol_get_packed_batch(const gol_handle *hs, size_t n, uint64_t *words, size_t
     if (rc) return rc;
     if ((int64_t)nwords != P->nwords)
         return fail(GOL_EINVAL, "nwords = %zu, the boards hold %lld words", nwords, (long long)P->nwords);
-    uint64_t *dst = (uint64_t *)mapped_host_pointer(words);
+    uint64_t *dst = (uint64_t *)mapped_host_pointer(words, *P);
     std::unique_ptr<Scratch> st;
     if (!dst) {
         st.reset(new Scratch(nwords * 8));

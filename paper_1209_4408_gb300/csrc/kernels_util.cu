@@ -316,36 +316,28 @@ __global__ void convert_kernel(const uint64_t *src, uint64_t *dst, int64_t n, bo
     }
 }
 
-// One warp transposes the 64 x 64 cell tile whose rows are [64 ti, 64 ti + 64)
-// and whose columns are word tj of `src` (src_w words per row) into rows
-// [64 tj, 64 tj + 64), word ti of `dst` (dst_w words per row).  Bit j of
-// output row 64 tj + j's word is gathered from the 64 input rows with two
-// warp ballots.  from_res / to_res convert words from / to the resident layout.
-__device__ __forceinline__ void transpose_tile(const uint64_t *__restrict__ src, int64_t src_w, int64_t ti,
-                                               int64_t tj, uint64_t *__restrict__ dst, int64_t dst_w,
-                                               bool from_res, bool to_res) {
+// A warp transposes a 64 x 64 bit matrix held as lane l: a = row l,
+// b = row l + 32 (bit j of a row = column j); afterwards lane l holds rows l
+// and l + 32 of the transpose.  Six rounds of masked block swaps (32-row
+// blocks within a lane, then 16, 8, 4, 2, 1 between lanes l and l ^ j).
+__device__ __forceinline__ void transpose64_lanes(uint64_t &a, uint64_t &b) {
     const int lane = threadIdx.x & 31;
-    uint64_t a = src[(64 * ti + lane) * src_w + tj];
-    uint64_t b = src[(64 * ti + 32 + lane) * src_w + tj];
-    if (from_res) {
-        a = to_interchange(a);
-        b = to_interchange(b);
+    uint64_t m = 0x00000000FFFFFFFFull;
+    const uint64_t t = ((a >> 32) ^ b) & m;
+    a ^= t << 32;
+    b ^= t;
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        m ^= m << j;
+        const uint64_t pa = __shfl_xor_sync(0xffffffffu, a, j), pb = __shfl_xor_sync(0xffffffffu, b, j);
+        if (lane & j) {
+            a ^= ((pa >> j) ^ a) & m;
+            b ^= ((pb >> j) ^ b) & m;
+        } else {
+            a ^= (((a >> j) ^ pa) & m) << j;
+            b ^= (((b >> j) ^ pb) & m) << j;
+        }
     }
-    uint64_t out_a = 0, out_b = 0;   // output rows 64 tj + lane and 64 tj + 32 + lane
-#pragma unroll 8
-    for (int j = 0; j < 64; ++j) {
-        const uint32_t lo = __ballot_sync(0xffffffffu, (uint32_t)(a >> j) & 1u);
-        const uint32_t hi = __ballot_sync(0xffffffffu, (uint32_t)(b >> j) & 1u);
-        const uint64_t w = (uint64_t)lo | ((uint64_t)hi << 32);
-        if (j == lane) out_a = w;
-        if (j == lane + 32) out_b = w;
-    }
-    if (to_res) {
-        out_a = to_resident(out_a);
-        out_b = to_resident(out_b);
-    }
-    dst[(64 * tj + lane) * dst_w + ti] = out_a;
-    dst[(64 * tj + 32 + lane) * dst_w + ti] = out_b;
 }
 
 // One block of 256 threads (8 warps) moves a super-tile of kSuper x kSuper
@@ -354,7 +346,7 @@ __device__ __forceinline__ void transpose_tile(const uint64_t *__restrict__ src,
 // (src_rows / 64) words.  Super-tile (si, sj) covers tile rows
 // ti in [8 si, 8 si + 8) and tile columns tj in [8 sj, 8 sj + 8): warp w
 // reads rows 64 (8 si + w) + lane and + 32, words 8 sj .. 8 sj + 7 of each,
-// transposes its tiles with ballots into shared memory, and the block then
+// transposes its tiles (transpose64_lanes) into shared memory, and the block then
 // writes output rows 64 tj + r, words 8 si .. 8 si + 7.  Tiles past the
 // edges of the board are skipped.  Every thread of the block must call it.
 __device__ void transpose_super(const uint64_t *__restrict__ src, int64_t src_rows, int64_t src_w,
@@ -376,17 +368,9 @@ __device__ void transpose_super(const uint64_t *__restrict__ src, int64_t src_ro
 #pragma unroll
         for (int k = 0; k < kSuper; ++k) {
             if (k >= nk) break;
-            const uint64_t x = from_res ? to_interchange(a[k]) : a[k];
-            const uint64_t y = from_res ? to_interchange(b[k]) : b[k];
-            uint64_t out_a = 0, out_b = 0;   // output rows 64 tj + lane and 64 tj + 32 + lane
-#pragma unroll 8
-            for (int j = 0; j < 64; ++j) {
-                const uint32_t lo = __ballot_sync(0xffffffffu, (uint32_t)(x >> j) & 1u);
-                const uint32_t hi = __ballot_sync(0xffffffffu, (uint32_t)(y >> j) & 1u);
-                const uint64_t v = (uint64_t)lo | ((uint64_t)hi << 32);
-                if (j == lane) out_a = v;
-                if (j == lane + 32) out_b = v;
-            }
+            uint64_t out_a = from_res ? to_interchange(a[k]) : a[k];
+            uint64_t out_b = from_res ? to_interchange(b[k]) : b[k];
+            transpose64_lanes(out_a, out_b);   // now output rows 64 tj + lane and 64 tj + 32 + lane
             sm[k][lane][w] = to_res ? to_resident(out_a) : out_a;
             sm[k][lane + 32][w] = to_res ? to_resident(out_b) : out_b;
         }
@@ -408,26 +392,15 @@ __global__ void orient_super_kernel(const uint64_t *__restrict__ src, uint64_t *
     transpose_super(src, src_rows, src_w, dst, blockIdx.x / nsj, blockIdx.x % nsj, !to_res, to_res);
 }
 
-// R x W interchange words -> resident storage: (64 W) x (R / 64) when
-// transposed, else R x W.  Reverse direction with to_res = false.
+// R x W interchange words <-> resident storage in the same orientation
+// (transposed boards go through orient_super_kernel).
 __global__ void orient_kernel(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, int64_t R, int64_t W,
-                              bool transposed, bool to_res) {
-    if (!transposed) {
-        const int64_t n = R * W;
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-             i += (int64_t)gridDim.x * blockDim.x) {
-            const uint64_t w = src[i];
-            dst[i] = to_res ? to_resident(w) : to_interchange(w);
-        }
-        return;
+                              bool to_res) {
+    const int64_t n = R * W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t w = src[i];
+        dst[i] = to_res ? to_resident(w) : to_interchange(w);
     }
-    // to_res: src is the board (R rows, W words); dst the stored transpose.
-    // from resident: src is the stored transpose (64 W rows, R / 64 words).
-    const int64_t rows_t = to_res ? R / 64 : W, cols_t = to_res ? W : R / 64;
-    const int64_t src_w = to_res ? W : R / 64, dst_w = to_res ? R / 64 : W;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-    for (int64_t t = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32; t < rows_t * cols_t; t += warps)
-        transpose_tile(src, src_w, t / cols_t, t % cols_t, dst, dst_w, !to_res, to_res);
 }
 
 // --- many boards <-> one contiguous staging buffer ----------------------------
@@ -540,7 +513,7 @@ cudaError_t launch_orient(const uint64_t *src, uint64_t *dst, int64_t R, int64_t
         const int64_t nsuper = ((R / 64 + kSuper - 1) / kSuper) * ((W + kSuper - 1) / kSuper);
         orient_super_kernel<<<(unsigned)nsuper, kBlock, 0, s>>>(src, dst, R, W, to_res);
     } else {
-        orient_kernel<<<grid_for(R * W, kBlock, 1 << 16), kBlock, 0, s>>>(src, dst, R, W, false, to_res);
+        orient_kernel<<<grid_for(R * W, kBlock, 1 << 16), kBlock, 0, s>>>(src, dst, R, W, to_res);
     }
     return cudaGetLastError();
 }
