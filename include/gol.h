@@ -207,6 +207,12 @@ const char *gol_last_error(void);
  *   GOL_OPT_ZERO_COPY      1 (default): many-board transfers read and write
  *                          pinned host buffers in place; 0: always through a
  *                          device staging buffer and cudaMemcpyAsync
+ *   GOL_OPT_CRITICAL_PERMILLE  a queued pass whose unit still has at least
+ *                          this permille of the longest chain of passes ahead
+ *                          of it is critical: idle warps take critical passes
+ *                          first (0: one first-in first-out queue for all
+ *                          passes; -1, the default: 500 when a launch steps
+ *                          several boards, 0 for one board)
  *   GOL_OPT_BYTE_CLUSTER   1 (default): a byte board whose rows fit the
  *                          shared memory of one thread-block cluster (8 CTAs,
  *                          2 x ceil(rows / 8) x cols <= 227 KiB) runs all its
@@ -222,6 +228,7 @@ const char *gol_last_error(void);
 #define GOL_OPT_PIPELINE 7
 #define GOL_OPT_ZERO_COPY 8
 #define GOL_OPT_BYTE_CLUSTER 9
+#define GOL_OPT_CRITICAL_PERMILLE 10
 int gol_set_option(int key, int64_t value);
 int gol_get_option(int key, int64_t *value);
 

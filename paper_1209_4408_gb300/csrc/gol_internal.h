@@ -60,7 +60,8 @@ struct UnitDesc {
     int32_t mode;
     int32_t nnb;      // neighbour units (same board), whose passes bound this one's
     int32_t nb[kMaxNeighbours];
-    int32_t pad;
+    int32_t cost;     // row iterations of a pass of the board's tallest unit (H + 2K), the same
+                      // for all units of a board: a pass's share of the rest of its chain
 };
 
 // What a warp needs to run a pass of one unit, in one 128-byte record:
@@ -74,7 +75,8 @@ struct __align__(128) UnitRun {
     int32_t board, R, W, npass, gens, nunits, cur;
     int32_t r0, r_end, H, S, w0, U, mode, nnb;
     int32_t nb[kMaxNeighbours];
-    int32_t pad[3];
+    int32_t cost;      // UnitDesc::cost
+    int32_t pad[2];
 };
 static_assert(sizeof(UnitRun) == 128, "UnitRun is one 128-byte line");
 
@@ -85,13 +87,23 @@ struct PersistArgs {
     UnitRun *run;       // [nunits] per-launch unit records (sched_init_kernel)
     int32_t *next_pass; // [nunits] the pass a queued unit runs next (set when it is claimed)
     int32_t *join;      // [2 * nunits] join counters, one per pass parity
-    int32_t *ring;      // [total_tasks] work queue, -1 = empty slot
-    int32_t *ctr;       // [0] head ticket, [1] tail slot, [2] tasks completed, [3] status,
+    int32_t *ring;      // [total_tasks] work queues, -1 = empty slot: the critical ring
+                        // [0, hi_cap), then the other ring [hi_cap, total_tasks)
+    int32_t *qctr;      // 128-byte line: [0] critical head, [1] critical tail,
+                        // [2] other ring's tickets, [3] other ring's tail
+    int32_t *ctr;       // [2] tasks completed, [3] status,
                         // [4 + b] units of board b that finished all passes
     int32_t *sticky;    // process-wide error word read by synchronising calls
     int32_t nunits;
     int32_t total_tasks;
     int64_t timeout_ns; // bounded waits give up after this long without progress
+    int64_t hi_thr;     // a pass is critical when (npass - pass + 1) * cost >= hi_thr
+    int32_t hi_cap;     // critical passes of the launch (the critical ring's size)
+    int32_t hi_init;    // first passes in the critical ring at launch (units 0 .. hi_init - 1
+                        // of init_order), the rest in the other ring
+    int32_t nwarps;     // warps of the launch; warp w < hi_init starts with critical slot w
+    int32_t pad;
+    const int32_t *init_order;   // [nunits] units by ring: critical first passes, then the others
 };
 
 // One board of a many-board transfer: `nwords` words of the board buffer

@@ -20,7 +20,7 @@ int grid_for(int64_t n, int block = kBlock, int64_t cap = 1 << 20) {
 
 // --- scheduler state ------------------------------------------------------
 __global__ void sched_init_kernel(PersistArgs a, int nboards) {
-    const int64_t n = max(max((int64_t)a.nunits, (int64_t)a.total_tasks), (int64_t)nboards);
+    const int64_t n = max(max((int64_t)a.nunits, (int64_t)a.total_tasks), (int64_t)max(nboards, 32));
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (i < a.nunits) {
@@ -46,17 +46,34 @@ __global__ void sched_init_kernel(PersistArgs a, int nboards) {
             r.mode = u.mode;
             r.nnb = u.nnb;
             for (int k = 0; k < kMaxNeighbours; ++k) r.nb[k] = u.nb[k];
-            r.pad[0] = r.pad[1] = r.pad[2] = 0;
+            r.cost = u.cost;
+            r.pad[0] = r.pad[1] = 0;
             a.run[i] = r;
             a.next_pass[i] = 1;            // every unit's first pass is queued below
             a.join[2 * i] = u.nnb + 1;     // join counters of both pass parities count down
             a.join[2 * i + 1] = u.nnb + 1; // the completions a pass waits for
         }
-        if (i < a.total_tasks) a.ring[i] = i < a.nunits ? (int32_t)i : -1;
+        if (i < a.total_tasks) {
+            // critical ring: its first hi_init slots; other ring: its first nunits - hi_init
+            int32_t v = -1;
+            if (i < a.hi_cap) {
+                if (i < a.hi_init) v = a.init_order[i];
+            } else if (i - a.hi_cap < a.nunits - a.hi_init) {
+                v = a.init_order[a.hi_init + (i - a.hi_cap)];
+            }
+            a.ring[i] = v;
+        }
         if (i < nboards) a.ctr[4 + i] = 0;
+        if (i < 32) {
+            int32_t v = 0;
+            if (i == 0) v = min(a.hi_init, a.nwarps);    // critical tickets: past the passes dealt at launch
+            if (i == 1) v = a.hi_init;
+            if (i == 3) v = a.nunits - a.hi_init;
+            a.qctr[i] = v;
+        }
         if (i == 0) {
-            a.ctr[0] = 0;         // next ticket
-            a.ctr[1] = a.nunits;  // next free slot
+            a.ctr[0] = 0;
+            a.ctr[1] = 0;
             a.ctr[2] = 0;         // tasks completed
             a.ctr[3] = 0;         // status
         }
@@ -473,7 +490,7 @@ __global__ void int_probe_kernel(unsigned *sink, int iters) {
 }  // namespace
 
 cudaError_t launch_sched_init(const PersistArgs &a, int nboards, cudaStream_t s) {
-    const int64_t n = max(max((int64_t)a.nunits, (int64_t)a.total_tasks), (int64_t)max(nboards, 1));
+    const int64_t n = max(max((int64_t)a.nunits, (int64_t)a.total_tasks), (int64_t)max(nboards, 32));
     sched_init_kernel<<<grid_for(n, kBlock, 4096), kBlock, 0, s>>>(a, nboards);
     return cudaGetLastError();
 }

@@ -651,49 +651,124 @@ __device__ __forceinline__ int pass_gens(const UnitRun &r, int pass) {
     return base + (pass <= rem ? 1 : 0);
 }
 
-// Lane 0: wait for queue slot t.  Returns the unit id, or -1 when all work
-// is done or the launch failed (status set).  The slot is polled with one
-// acquire load per round; the launch status, the completion count and the
-// clock are checked every eighth round.
-static __device__ int wait_for_slot(const PersistArgs &A, int t) {
-    uint64_t t_last = global_ns();
-    int seen = ld_acquire(&A.ctr[2]);
+__device__ __forceinline__ int ld_relaxed(const int32_t *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int2 ld_relaxed_v2(const int32_t *p) {
+    int2 v;
+    asm volatile("ld.relaxed.gpu.global.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void set_status(const PersistArgs &A, int code) {
+    atomicCAS(&A.ctr[3], 0, code);
+    atomicCAS(A.sticky, 0, code);
+}
+
+// Lane 0: wait until a queue slot that has been handed to this warp holds
+// its unit (the filler took the slot from the ring's tail and is about to
+// store it).  Returns the unit, or -1 if the launch failed or the wait gave up.
+static __device__ int wait_slot(const PersistArgs &A, const int32_t *slot) {
+    const uint64_t t0 = global_ns();
     unsigned ns = 32;
     for (long long spin = 0; spin < (1ll << 32); ++spin) {
-        const int v = ld_acquire(&A.ring[t]);
+        const int v = ld_acquire(slot);
         if (v >= 0) return v;
         if ((spin & 7) == 7) {
-            if (ld_acquire(&A.ctr[3]) != 0) return -1;
-            const int c = ld_acquire(&A.ctr[2]);
-            if (c >= A.total_tasks) return -1;
-            const uint64_t now = global_ns();
-            if (c != seen) {
-                seen = c;
-                t_last = now;
-            } else if (now - t_last > (uint64_t)A.timeout_ns) {
-                atomicCAS(&A.ctr[3], 0, GOL_ETIMEOUT);
-                atomicCAS(A.sticky, 0, GOL_ETIMEOUT);
+            if (ld_relaxed(&A.ctr[3]) != 0) return -1;
+            if (global_ns() - t0 > (uint64_t)A.timeout_ns) {
+                set_status(A, GOL_ETIMEOUT);
                 return -1;
             }
         }
         __nanosleep(ns);
         if (ns < 128) ns <<= 1;
     }
-    atomicCAS(&A.ctr[3], 0, GOL_ETIMEOUT);
-    atomicCAS(A.sticky, 0, GOL_ETIMEOUT);
+    set_status(A, GOL_ETIMEOUT);
     return -1;
 }
 
-__device__ __forceinline__ void enqueue(const PersistArgs &A, int v) {
-    const int slot = atomicAdd(&A.ctr[1], 1);
-    st_release(&A.ring[slot], v);
+// Queues unit v for its next pass, rem = (npass - pass + 1) * cost being the
+// rest of its chain: into the critical ring when rem >= hi_thr, else into
+// the other one.  Each ring has a slot for every pass of its kind.
+__device__ __forceinline__ void enqueue(const PersistArgs &A, int v, int64_t rem) {
+    const bool hi = rem >= A.hi_thr;
+    const int slot = atomicAdd(&A.qctr[hi ? 1 : 3], 1);
+    const int64_t base = hi ? 0 : A.hi_cap, cap = hi ? A.hi_cap : A.total_tasks - A.hi_cap;
+    if (slot < cap)
+        st_release(&A.ring[base + slot], v);
+    else
+        set_status(A, GOL_ECUDA);              // the planner's ring sizes were wrong
 }
 
-__device__ __forceinline__ int ld_relaxed(const int32_t *p) {
-    int v;
-    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
+// Lane 0: take the next pass to run.  A warp may hold one ticket of each
+// ring (`tk[0]` critical, `tk[1]` other), taken with atomicAdd and kept until
+// its slot is filled (or the launch ends), even while the warp runs other
+// passes: a ticket is a promise to run what lands in its slot.  The warp
+// takes a critical ticket when the critical ring shows queued passes (one
+// load of its head and tail; the ticket may land past them and then waits
+// for the next critical pass), otherwise an other-ring ticket, and serves
+// whichever slot fills first, the critical one when both have.  Returns the
+// unit (its pass is in next_pass), or -1 when every pass of the launch has
+// completed or the launch failed.  Bounded: no completed pass for
+// timeout_ns sets GOL_ETIMEOUT.
+__device__ __forceinline__ int ticket_unit(const PersistArgs &A, int (&tk)[2]) {
+    const int lo_cap = A.total_tasks - A.hi_cap;
+    if (tk[0] >= 0 && tk[0] < A.hi_cap) {
+        const int v = ld_acquire(&A.ring[tk[0]]);
+        if (v >= 0) {
+            tk[0] = -1;
+            return v;
+        }
+    }
+    if (tk[1] >= 0 && tk[1] < lo_cap) {
+        const int v = ld_acquire(&A.ring[A.hi_cap + tk[1]]);
+        if (v >= 0) {
+            tk[1] = -1;
+            return v;
+        }
+    }
+    return -1;
 }
+
+static __device__ int take_work(const PersistArgs &A, int (&tk)[2]) {
+    uint64_t t_last = global_ns();
+    int seen = -1;
+    unsigned ns = 32;
+    for (long long spin = 0; spin < (1ll << 32); ++spin) {
+        const int v = ticket_unit(A, tk);
+        if (v >= 0) return v;
+        if (tk[0] < 0 && A.hi_cap > 0 && (spin & 7) == 0) {
+            const int2 ht = ld_relaxed_v2(&A.qctr[0]);
+            if (ht.x < ht.y) {
+                tk[0] = atomicAdd(&A.qctr[0], 1);
+                continue;
+            }
+        }
+        if (tk[1] < 0) {
+            tk[1] = atomicAdd(&A.qctr[2], 1);
+            continue;
+        }
+        if ((spin & 7) == 7) {
+            const int done = ld_relaxed(&A.ctr[2]);
+            if (ld_relaxed(&A.ctr[3]) != 0 || done >= A.total_tasks) return -1;
+            const uint64_t now = global_ns();
+            if (done != seen) {
+                seen = done;
+                t_last = now;
+            } else if (now - t_last > (uint64_t)A.timeout_ns) {
+                set_status(A, GOL_ETIMEOUT);
+                return -1;
+            }
+        }
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+    }
+    set_status(A, GOL_ETIMEOUT);
+    return -1;
+}
+
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ void red_add(int32_t *p, int v) {
     asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -747,7 +822,7 @@ __device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pa
     const int next = __shfl_sync(kFull, v, leader);
     if (ready && lane != leader) {
         A.next_pass[v] = pass + 1;            // published by the queue slot's release
-        enqueue(A, v);
+        enqueue(A, v, (int64_t)(r.npass - pass) * r.cost);
     }
     return next;
 }
@@ -766,26 +841,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32,
 persistent_step_kernel(const PersistArgs A) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    int u = -1, pass = 0;
+    const int w = blockIdx.x * kWarpsPerBlock + (int)(threadIdx.x >> 5);
+    // warp w < hi_init starts with the critical ring's slot w (pass 1)
+    int u = w < min(A.hi_init, A.nwarps) ? A.ring[w] : -1, pass = 1;
+    int tk[2] = {-1, -1};    // lane 0: the tickets this warp holds (critical, other)
     for (;;) {
         if (u < 0) {
-            int t = 0;
-            if (lane == 0) t = atomicAdd(&A.ctr[0], 1);
-            t = __shfl_sync(kFull, t, 0);
-            if (t >= A.total_tasks) return;
-            int v = -1;
+            int v = -1, p = 0;
             if (lane == 0) {
-                v = wait_for_slot(A, t);
-                // written before the slot by the thread that claimed v; the
+                v = take_work(A, tk);
+                // written before the slot by the thread that queued v; the
                 // slot's acquire load orders this read after it
-                if (v >= 0) pass = A.next_pass[v];
+                if (v >= 0) p = A.next_pass[v];
             }
-            v = __shfl_sync(kFull, v, 0);
-            if (v < 0) return;
-            pass = __shfl_sync(kFull, pass, 0);
-            u = v;
-        } else {
-            ++pass;          // continuing in this warp: the next pass of a unit of the same board
+            u = __shfl_sync(kFull, v, 0);
+            if (u < 0) return;
+            pass = __shfl_sync(kFull, p, 0);
         }
         const UnitRun r = A.run[u];
         const int my_nb = (lane >= 1 && lane <= kMaxNeighbours) ? A.run[u].nb[lane - 1] : u;
@@ -815,7 +886,29 @@ persistent_step_kernel(const PersistArgs A) {
         // then the warp barrier)
         fence_acq_rel_gpu();
         __syncwarp();
-        u = complete_pass(A, u, pass, r, my_nb);
+        const int next = complete_pass(A, u, pass, r, my_nb);
+        // a filled ticket runs before a continuation in this warp, which is
+        // queued instead (so that no ticket waits on a chain)
+        int take = -1, tpass = 0;
+        if (lane == 0 && next >= 0 && (tk[0] >= 0 || tk[1] >= 0)) {
+            const int v = ticket_unit(A, tk);
+            if (v >= 0) {
+                A.next_pass[next] = pass + 1;
+                enqueue(A, next, (int64_t)(r.npass - pass) * r.cost);
+                take = v;
+                tpass = A.next_pass[v];
+            }
+        }
+        take = __shfl_sync(kFull, take, 0);
+        if (take >= 0) {
+            u = take;
+            pass = __shfl_sync(kFull, tpass, 0);
+        } else if (next >= 0) {
+            u = next;
+            ++pass;          // continuing in this warp: the next pass of a unit of the same board
+        } else {
+            u = -1;
+        }
     }
 }
 

@@ -42,6 +42,7 @@ GOL_OPT_CHAIN_PERMILLE = 6
 GOL_OPT_PIPELINE = 7
 GOL_OPT_ZERO_COPY = 8
 GOL_OPT_BYTE_CLUSTER = 9
+GOL_OPT_CRITICAL_PERMILLE = 10
 
 # every symbol declared in include/gol.h
 EXPORTED = (
