@@ -827,17 +827,22 @@ __device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pa
     return next;
 }
 
-// Blocks per SM the register allocation must allow (GOL_MIN_BLOCKS at build
-// time; 1 leaves the choice to the compiler).
+// Blocks per SM the register allocation must allow (GOL_MIN_BLOCKS for
+// K = 4..6 and GOL_MIN_BLOCKS_K8 for K = 8 at build time; 1 leaves the
+// choice to the compiler).
 #ifndef GOL_MIN_BLOCKS
 #define GOL_MIN_BLOCKS 1
+#endif
+#ifndef GOL_MIN_BLOCKS_K8
+#define GOL_MIN_BLOCKS_K8 1
 #endif
 
 // The skewed variant keeps K more register pairs; at K = 6 it is held to
 // six blocks (three warps per scheduler) per SM.
 template <int K, bool TORUS, int VARIANT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32,
-                                  (K >= 4 && K <= 6) ? (VARIANT == 2 && GOL_MIN_BLOCKS < 6 ? 6 : GOL_MIN_BLOCKS) : 1)
+                                  (K >= 4 && K <= 6) ? (VARIANT == 2 && GOL_MIN_BLOCKS < 6 ? 6 : GOL_MIN_BLOCKS)
+                                                     : (K == 8 ? GOL_MIN_BLOCKS_K8 : 1))
 persistent_step_kernel(const PersistArgs A) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
