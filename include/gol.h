@@ -202,8 +202,11 @@ const char *gol_last_error(void);
  *                          1 = it rotates them by renaming (fewer issued
  *                          instructions), 2 = renaming with skewed stages
  *                          (stage g works one row behind stage g - 1, so the
- *                          stages of a row step are independent), -1
- *                          (default) = 1; results are identical
+ *                          stages of a row step are independent), 3 = 1 held
+ *                          to three warps per scheduler at 8 generations per
+ *                          pass, -1 (default) = 3 for 8 generations per pass
+ *                          and many units per warp, else 1; results are
+ *                          identical
  *   GOL_OPT_ZERO_COPY      1 (default): many-board transfers read and write
  *                          pinned host buffers in place; 0: always through a
  *                          device staging buffer and cudaMemcpyAsync

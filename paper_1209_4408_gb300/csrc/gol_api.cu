@@ -249,7 +249,16 @@ int supported_k(int k) {
 // Kernel variant of a plan: the window rotation by renaming (1) measured
 // faster than register moves (0) on both the 4096-board batch and a 16384^2
 // board once the join-counter scheduler removed most per-pass overhead.
-int plan_variant(size_t) { return g_opt_variant >= 0 ? (int)g_opt_variant : 1; }
+// At K = 8 a launch with at least 8 units per warp of the unrestricted
+// kernel (two warps per scheduler) takes variant 3, held to three warps per
+// scheduler: measured on a 131072^2 board (35k units) 45.2k against 39.8k
+// GCUPS, while a 16384^2 board (2304 units) keeps 35.7k with variant 1
+// against 32.5k with variant 3.
+int plan_variant(int K, int64_t units_estimate) {
+    if (g_opt_variant >= 0) return (int)g_opt_variant;
+    if (K == 8 && units_estimate >= 8LL * g_dev.sms * 8) return 3;
+    return 1;
+}
 
 cudaError_t occupancy_for(int K, bool torus, int v, int *bps) {
     switch (K) {
@@ -448,7 +457,13 @@ int build_plan(Plan &P) {
         }
     }
     P.K = supported_k(std::max(1, K));
-    P.variant = plan_variant(n);
+    int64_t units_estimate = 0;    // with the tuned tile rows, before any chain cap
+    for (size_t i = 0; i < n; ++i) {
+        const UnitGrid ug = unit_grid(P.hs[i]->srows, P.hs[i]->swords, P.K,
+                                      std::max(1, tune_lookup(P.hs[i]->srows, P.hs[i]->swords * 64).rows));
+        units_estimate += (int64_t)ug.nb * ug.nt;
+    }
+    P.variant = plan_variant(P.K, units_estimate);
     int bps = 1;
     cudaError_t e = occupancy_for(P.K, P.torus, P.variant, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -1302,7 +1317,7 @@ int gol_set_option(int key, int64_t v) {
             g_opt_chain = v;
             return GOL_OK;
         case GOL_OPT_PIPELINE:
-            if (v < -1 || v > 2) return fail(GOL_EINVAL, "pipeline variant must be -1, 0, 1 or 2");
+            if (v < -1 || v > 3) return fail(GOL_EINVAL, "pipeline variant must be -1, 0, 1, 2 or 3");
             g_opt_variant = v;
             return GOL_OK;
         case GOL_OPT_ZERO_COPY:
@@ -1502,7 +1517,7 @@ extern "C" int gol_step_packed_noalloc(uint64_t *d_board, uint64_t *d_spare, int
     const TuneEntry te = tune_lookup(rows, cols);
     const int K = supported_k(std::max(1, te.k));
     int bps = 1;
-    const int variant = plan_variant(1);
+    const int variant = plan_variant(K, 0);   // at most 4096 units: never the held-down variant
     CU(occupancy_for(K, torus != 0, variant, &bps));
     const int64_t slots = (int64_t)sms * std::max(1, bps) * kWarpsPerBlock;
     const int64_t npass_all = (generations + K - 1) / K;

@@ -838,11 +838,13 @@ __device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pa
 #endif
 
 // The skewed variant keeps K more register pairs; at K = 6 it is held to
-// six blocks (three warps per scheduler) per SM.
+// six blocks (three warps per scheduler) per SM.  Variant 3 is variant 1 held
+// to six blocks per SM at K = 8 (168 registers instead of 185: three warps
+// per scheduler instead of two), for launches with many units per warp.
 template <int K, bool TORUS, int VARIANT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32,
                                   (K >= 4 && K <= 6) ? (VARIANT == 2 && GOL_MIN_BLOCKS < 6 ? 6 : GOL_MIN_BLOCKS)
-                                                     : (K == 8 ? GOL_MIN_BLOCKS_K8 : 1))
+                                                     : (K == 8 ? (VARIANT == 3 ? 6 : GOL_MIN_BLOCKS_K8) : 1))
 persistent_step_kernel(const PersistArgs A) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -875,7 +877,7 @@ persistent_step_kernel(const PersistArgs A) {
                 run_unit_pass_moves<K, TORUS, false>(r, src, dst, K);
             else
                 run_unit_pass_moves<K, TORUS, true>(r, src, dst, kk);
-        } else if (VARIANT == 1) {
+        } else if (VARIANT == 1 || VARIANT == 3) {
             if (kk == K)
                 run_unit_pass<K, TORUS, false>(r, src, dst, K);
             else
@@ -924,11 +926,16 @@ cudaError_t launch_persistent_impl(const PersistArgs &a, bool torus, int variant
             persistent_step_kernel<K, true, 0><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
         else
             persistent_step_kernel<K, false, 0><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
-    } else if (variant == 1) {
+    } else if (variant == 1 || (variant == 3 && K != 8)) {
         if (torus)
             persistent_step_kernel<K, true, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
         else
             persistent_step_kernel<K, false, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+    } else if (variant == 3) {
+        if (torus)
+            persistent_step_kernel<K, true, (K == 8 ? 3 : 1)><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+        else
+            persistent_step_kernel<K, false, (K == 8 ? 3 : 1)><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
     } else {
         if (torus)
             persistent_step_kernel<K, true, 2><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
@@ -944,9 +951,14 @@ cudaError_t persistent_occupancy_impl(bool torus, int variant, int *bps) {
     if (variant == 0)
         return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, 0>, t, 0)
                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, 0>, t, 0);
-    if (variant == 1)
+    if (variant == 1 || (variant == 3 && K != 8))
         return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, 1>, t, 0)
                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, 1>, t, 0);
+    if (variant == 3)
+        return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, (K == 8 ? 3 : 1)>,
+                                                                     t, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, (K == 8 ? 3 : 1)>,
+                                                                     t, 0);
     return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, 2>, t, 0)
                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, 2>, t, 0);
 }

@@ -167,7 +167,7 @@ def test_packed_random_shapes(gol, opts, R, C, torus):
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 8, 16])
 @pytest.mark.parametrize("rows", [1, 8, 64, 1000])
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_packed_result_independent_of_pass_and_tile(gol, opts, k, rows, variant):
     R, C, G = 192, 2240, 23
     cells = synth.bernoulli_board(R, C, 0.5, 4242)
