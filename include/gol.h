@@ -94,10 +94,10 @@ int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords);
  * current states into one device buffer, copies it to `words` and
  * synchronises.  When `words` is page-locked memory registered with CUDA
  * (cudaHostAlloc, cudaHostRegister) and no board of the transfer is stored
- * transposed, the scatter / gather kernel reads or writes it in place, with
- * no staging copy (GOL_OPT_ZERO_COPY = 0 turns that off); otherwise the
- * words go through a device staging buffer.  Non-packed boards are
- * GOL_EINVAL. */
+ * transposed, the scatter / gather kernel reads or
+ * writes it in place, with no staging copy (GOL_OPT_ZERO_COPY = 0 turns
+ * that off); otherwise the words go through a device staging buffer.
+ * Non-packed boards are GOL_EINVAL. */
 int gol_set_packed_batch(const gol_handle *hs, size_t n, const uint64_t *words, size_t nwords);
 int gol_get_packed_batch(const gol_handle *hs, size_t n, uint64_t *words, size_t nwords);
 
