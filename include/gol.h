@@ -216,11 +216,16 @@ const char *gol_last_error(void);
  *                          first (0: one first-in first-out queue for all
  *                          passes; -1, the default: 500 when a launch steps
  *                          several boards, 0 for one board)
- *   GOL_OPT_BYTE_CLUSTER   1 (default): a byte board whose rows fit the
- *                          shared memory of one thread-block cluster (8 CTAs,
- *                          2 x ceil(rows / 8) x cols <= 227 KiB) runs all its
- *                          generations in one launch of that cluster; 0: one
- *                          launch per generation (graph replay when long)
+ *   GOL_OPT_BYTE_CLUSTER   1 (default): a byte board whose cells fit, one
+ *                          bit each, in the shared memory of a thread-block
+ *                          cluster of up to 8 CTAs (two buffers of
+ *                          ceil(rows / n) rows of ceil(cols / 64) words per
+ *                          CTA within 227 KiB) runs all its generations in
+ *                          one launch of such a cluster (n: the smallest
+ *                          that fits, doubled while a CTA would hold more
+ *                          than 256 words); 2, 4, 8: that cluster size when
+ *                          it fits; 0: one launch per generation (graph
+ *                          replay when long)
  * Unknown keys or values are GOL_EINVAL. */
 #define GOL_OPT_GENS_PER_PASS 1
 #define GOL_OPT_TILE_ROWS 2

@@ -717,7 +717,7 @@ int step_bytes(gol_handle h, int64_t G) {
         while (G > 0) {
             const int g = (int)std::min<int64_t>(G, kByteClusterGensPerLaunch);
             cudaError_t e = launch_byte_cluster((const uint8_t *)h->buf[h->cur], (uint8_t *)h->buf[h->cur ^ 1], h->rows,
-                                                h->cols, h->torus, g, g_stream);
+                                                h->cols, h->torus, g, (int)g_opt_byte_cluster, g_stream);
             if (e != cudaSuccess) return cuda_fail(e, "byte cluster launch");
             h->cur ^= 1;
             h->generation += g;
@@ -1327,7 +1327,7 @@ int gol_set_option(int key, int64_t v) {
             g_opt_zero_copy = v;
             return GOL_OK;
         case GOL_OPT_BYTE_CLUSTER:
-            if (v < 0 || v > 1) return fail(GOL_EINVAL, "byte cluster must be 0 or 1");
+            if (v < 0 || v > 8 || (v > 1 && (v & (v - 1)))) return fail(GOL_EINVAL, "byte cluster must be 0, 1, 2, 4 or 8");
             g_opt_byte_cluster = v;
             return GOL_OK;
         case GOL_OPT_CRITICAL_PERMILLE:

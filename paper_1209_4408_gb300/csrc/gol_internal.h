@@ -195,7 +195,9 @@ cudaError_t launch_popcount_bytes(const uint8_t *cells, int64_t n, unsigned long
 constexpr int kByteClusterMax = 8;                 // CTAs per cluster (portable size)
 constexpr int64_t kByteClusterBytes = 227 * 1024;  // shared memory per CTA
 int byte_cluster_size(int64_t R, int64_t C);
-cudaError_t launch_byte_cluster(const uint8_t *in, uint8_t *out, int64_t R, int64_t C, int torus, int G,
+constexpr int64_t kByteWordsPerCta = 256;          // auto cluster size: words per CTA at most (if it can)
+int byte_cluster_choice(int64_t R, int64_t C, int want);
+cudaError_t launch_byte_cluster(const uint8_t *in, uint8_t *out, int64_t R, int64_t C, int torus, int G, int want,
                                 cudaStream_t s);
 cudaError_t launch_convert(const uint64_t *src, uint64_t *dst, int64_t n, bool to_res, cudaStream_t s);
 cudaError_t launch_scatter_boards(const CopyDesc *d, const int32_t *block_board, int64_t blocks, const uint64_t *staging,

@@ -580,17 +580,35 @@ int byte_cluster_size(int64_t R, int64_t C) {
     return 0;
 }
 
-cudaError_t launch_byte_cluster(const uint8_t *in, uint8_t *out, int64_t R, int64_t C, int torus, int G,
+// Cluster size used for a board: `want` when it is a power of two <= 8 that
+// fits (forced), else the smallest power of two that fits and leaves each CTA
+// at most kByteWordsPerCta words (more CTAs share the generation's work).
+int byte_cluster_choice(int64_t R, int64_t C, int want) {
+    const int nmin = byte_cluster_size(R, C);
+    if (nmin == 0) return 0;
+    const int64_t W = (C + 63) / 64;
+    if (want > 1) {
+        if ((want & (want - 1)) || want > kByteClusterMax || want > R || want < nmin) return nmin;
+        return want;
+    }
+    int n = nmin;
+    while (n < kByteClusterMax && 2 * n <= R && ((R + n - 1) / n) * W > kByteWordsPerCta) n *= 2;
+    return n;
+}
+
+cudaError_t launch_byte_cluster(const uint8_t *in, uint8_t *out, int64_t R, int64_t C, int torus, int G, int want,
                                 cudaStream_t s) {
-    const int n = byte_cluster_size(R, C);
+    const int n = byte_cluster_choice(R, C, want);
     if (n == 0 || G < 1) return cudaErrorInvalidValue;
     const int64_t hmax = (R + n - 1) / n, W = (C + 63) / 64;
     const size_t smem = (size_t)(2 * hmax * W * 8);
+    // one thread per word of a strip, in whole warps, 64 .. 1024
+    const unsigned threads = (unsigned)std::min<int64_t>(1024, std::max<int64_t>(64, (hmax * W + 31) / 32 * 32));
     if (n == 1) {
         cudaError_t e = cudaFuncSetAttribute(byte_resident_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        byte_resident_kernel<false><<<1, 1024, smem, s>>>(in, out, (int)R, (int)C, torus, G);
+        byte_resident_kernel<false><<<1, threads, smem, s>>>(in, out, (int)R, (int)C, torus, G);
         return cudaGetLastError();
     }
     cudaError_t e = cudaFuncSetAttribute(byte_resident_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -598,7 +616,7 @@ cudaError_t launch_byte_cluster(const uint8_t *in, uint8_t *out, int64_t R, int6
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)n, 1, 1);
-    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

@@ -87,15 +87,16 @@ def test_bytes_random_multi_gen(gol, R, C):
                     "bytes %dx%d" % (R, C))
 
 
-@pytest.mark.parametrize("cluster", [1, 0])
+@pytest.mark.parametrize("cluster", [1, 0, 2, 8])
 @pytest.mark.parametrize("R,C", [(1, 1), (2, 3), (9, 1), (7, 9), (16, 16), (33, 65), (100, 700), (960, 960),
                                  (1000, 1600), (1500, 1500), (2048, 2048), (3072, 3072)])
 def test_bytes_cluster_and_per_generation_paths(gol, cluster, R, C):
     # boards whose cells fit, one bit each, in a cluster's shared memory
     # (two buffers of ceil(R / n) rows of ceil(C / 64) words per CTA, n <= 8:
     # 2048 x 2048 does) run all generations in one cluster launch; 3072 x
-    # 3072 and option 0 take one launch per generation; both match the
-    # oracle, torus and bounded
+    # 3072 and option 0 take one launch per generation; options 2 and 8 force
+    # that many CTAs where they fit (each strip at least one row); all match
+    # the oracle, torus and bounded
     gol.gol_set_option(gol.GOL_OPT_BYTE_CLUSTER, cluster)
     try:
         cells = synth.bernoulli_board(R, C, 0.35, 7 * R + C)
@@ -242,6 +243,31 @@ def test_batch_equals_alone(gol):
         assert_same(got, oracle.run(c, s.gens), "batch board %d" % s.index)
         assert_same(got, run_gpu(gol, c, s.gens), "alone board %d" % s.index)
         assert b.generation() == s.gens
+
+
+@pytest.mark.parametrize("critical", [0, 1, 500, 1000])
+@pytest.mark.parametrize("k", [2, 6, 8])
+def test_batch_queue_settings(gol, opts, critical, k):
+    # the same results whatever share of the passes goes to the critical ring
+    # (none, nearly all, half, only the longest chain), with tiles short
+    # enough for many units per board and boards of one unit
+    specs = synth.batch_specs(30, seed=31 + k, side_hi=900, gen_lo=4, gen_hi=90)
+    gol.gol_set_option(gol.GOL_OPT_CRITICAL_PERMILLE, critical)
+    opts(k, 16)
+    try:
+        boards, cells = [], []
+        for s in specs:
+            c = synth.bernoulli_board(s.rows, s.cols, s.density, s.seed)
+            b = gol.Board(s.rows, s.cols)
+            b.set(c)
+            boards.append(b)
+            cells.append(c)
+        gol.step_batch(boards, [s.gens for s in specs])
+        for s, b, c in zip(specs, boards, cells):
+            assert_same(b.get(), oracle.run(c, s.gens), "critical %d K=%d board %d" % (critical, k, s.index))
+            b.close()
+    finally:
+        gol.gol_set_option(gol.GOL_OPT_CRITICAL_PERMILLE, -1)
 
 
 def test_batch_repeat_replays_graph(gol):
