@@ -42,8 +42,8 @@ extern "C" {
 #define GOL_EBUSY (-5)    /* the handle is in use by an unfinished batch                          */
 
 /* Board storage chosen at creation. */
-#define GOL_LAYOUT_AUTO 0   /* packed when cols % 64 == 0, else bytes                           */
-#define GOL_LAYOUT_PACKED 1 /* 64 cells per uint64 (cols % 64 == 0 required)                     */
+#define GOL_LAYOUT_AUTO 0   /* packed when cols % 64 == 0 or rows % 64 == 0, else bytes         */
+#define GOL_LAYOUT_PACKED 1 /* 64 cells per uint64 (cols % 64 == 0 or rows % 64 == 0 required)    */
 #define GOL_LAYOUT_BYTES 2  /* one uint8 per cell, any rows, cols >= 1                            */
 
 typedef struct gol_board *gol_handle;
@@ -56,7 +56,11 @@ typedef struct gol_board *gol_handle;
 int gol_create(int64_t rows, int64_t cols, int torus, gol_handle *out);
 
 /* As gol_create with an explicit layout (GOL_LAYOUT_*).  GOL_LAYOUT_PACKED
- * with cols % 64 != 0 is GOL_EINVAL. */
+ * needs cols % 64 == 0 or rows % 64 == 0 (else GOL_EINVAL).  A packed board
+ * whose width is not a multiple of 64 is stored transposed (words along the
+ * height); it steps like any packed board, but has no packed word layout:
+ * gol_set_packed / gol_get_packed (and their device and batch forms) are
+ * GOL_EINVAL for it, gol_set / gol_get / gol_get_region work. */
 int gol_create_ex(int64_t rows, int64_t cols, int torus, int layout, gol_handle *out);
 
 /* Frees the board's device memory after its stream's work has finished.
@@ -214,7 +218,7 @@ const char *gol_last_error(void);
  *                          this permille of the longest chain of passes ahead
  *                          of it is critical: idle warps take critical passes
  *                          first (0: one first-in first-out queue for all
- *                          passes; -1, the default: 500 when a launch steps
+ *                          passes; -1, the default: 750 when a launch steps
  *                          several boards, 0 for one board)
  *   GOL_OPT_BYTE_CLUSTER   1 (default): a byte board whose cells fit, one
  *                          bit each, in the shared memory of a thread-block

@@ -36,6 +36,10 @@ struct gol_board {
     // board's own rows x words.
     int transposed = 0;
     int64_t srows = 0, swords = 0;
+    // A packed board whose width is not a multiple of 64 (its height must
+    // be) is always stored transposed, so that its stored rows are whole
+    // words; it has no packed interchange layout (words = 0).
+    int odd_width = 0;
     // byte boards: captured graphs of 64 generations, per starting buffer
     cudaGraphExec_t byte_graph[2] = {nullptr, nullptr};
     cudaStream_t byte_graph_stream = nullptr;
@@ -82,7 +86,7 @@ int64_t g_opt_variant = -1;  // step kernel variant (see launch_persistent), -1 
 int64_t g_opt_zero_copy = 1; // many-board transfers read / write pinned host buffers in place
 int64_t g_opt_byte_cluster = 1; // byte boards that fit one cluster's shared memory step there
 int64_t g_opt_critical = -1;    // permille of the longest chain from which a queued pass is
-                                // critical; -1: 500 for several boards, none for one board
+                                // critical; -1: 750 for several boards, none for one board
 uint64_t g_serial = 0;
 
 struct DeviceState {
@@ -358,15 +362,16 @@ void set_board_cost(UnitDesc *us, int n, int K) {
 // by the ring of their first pass, critical first, each in unit (LPT) order,
 // into init_out[0 .. nunits).  Units of a board are consecutive; npass_of(b)
 // is board b's pass count.  Uses no dynamic memory.
-// Measured on the 4096-board batch: 500 permille 34.4k GCUPS, 250 34.0k,
-// none 33.7k; on one board (equal chains) it changes nothing and is off.
+// Measured on the 4096-board batch: 750 permille 34.9k GCUPS, 500 34.7k,
+// 350 34.2k, 250 34.0k, none 33.7k; on one board (equal chains) it changes
+// nothing and is off.
 template <typename NpassOf>
 void plan_rings(const UnitDesc *units, int nunits, size_t nboards, NpassOf npass_of, PersistArgs &a,
                 int32_t *init_out) {
     int64_t maxchain = 1;
     for (int u = 0; u < nunits; ++u)
         maxchain = std::max(maxchain, (int64_t)npass_of(units[u].board) * units[u].cost);
-    const int64_t permille = g_opt_critical >= 0 ? g_opt_critical : (nboards > 1 ? 500 : 0);
+    const int64_t permille = g_opt_critical >= 0 ? g_opt_critical : (nboards > 1 ? 750 : 0);
     a.hi_thr = permille > 0 ? std::max<int64_t>(1, (maxchain * permille + 999) / 1000) : INT64_MAX;
     int64_t hi_cap = 0;
     int32_t hi_init = 0;
@@ -806,11 +811,13 @@ int gol_create_ex(int64_t rows, int64_t cols, int torus, int layout, gol_handle 
     *out = nullptr;
     if (rows < 1 || cols < 1) return fail(GOL_EINVAL, "rows and cols must be >= 1 (got %lld x %lld)",
                                           (long long)rows, (long long)cols);
-    if (layout == GOL_LAYOUT_AUTO) layout = (cols % 64 == 0) ? GOL_LAYOUT_PACKED : GOL_LAYOUT_BYTES;
+    if (layout == GOL_LAYOUT_AUTO)
+        layout = (cols % 64 == 0 || rows % 64 == 0) ? GOL_LAYOUT_PACKED : GOL_LAYOUT_BYTES;
     if (layout != GOL_LAYOUT_PACKED && layout != GOL_LAYOUT_BYTES) return fail(GOL_EINVAL, "unknown layout %d", layout);
-    if (layout == GOL_LAYOUT_PACKED && cols % 64 != 0)
-        return fail(GOL_EINVAL, "packed layout needs cols %% 64 == 0 (cols = %lld)", (long long)cols);
-    if (layout == GOL_LAYOUT_PACKED && (rows > (int64_t(1) << 30) || cols / 64 > (int64_t(1) << 30)))
+    if (layout == GOL_LAYOUT_PACKED && cols % 64 != 0 && rows % 64 != 0)
+        return fail(GOL_EINVAL, "packed layout needs cols or rows a multiple of 64 (%lld x %lld)", (long long)rows,
+                    (long long)cols);
+    if (layout == GOL_LAYOUT_PACKED && (rows > (int64_t(1) << 30) || cols > (int64_t(1) << 30)))
         return fail(GOL_EINVAL, "board too large");
     int rc = ensure_device();
     if (rc) return rc;
@@ -819,15 +826,20 @@ int gol_create_ex(int64_t rows, int64_t cols, int torus, int layout, gol_handle 
     h->cols = cols;
     h->torus = torus ? 1 : 0;
     h->layout = layout;
-    h->words = layout == GOL_LAYOUT_PACKED ? cols / 64 : 0;
-    h->buf_bytes = layout == GOL_LAYOUT_PACKED ? (size_t)rows * (size_t)h->words * 8 : (size_t)rows * (size_t)cols;
+    h->odd_width = layout == GOL_LAYOUT_PACKED && cols % 64 != 0;
+    h->words = layout == GOL_LAYOUT_PACKED && !h->odd_width ? cols / 64 : 0;
+    h->buf_bytes = layout == GOL_LAYOUT_PACKED ? (size_t)rows * (size_t)cols / 8 : (size_t)rows * (size_t)cols;
     h->alloc_fn = g_alloc;
     h->free_fn = g_free;
     h->alloc_ctx = g_alloc_ctx;
     h->serial = ++g_serial;
     h->srows = rows;
     h->swords = h->words;
-    if (layout == GOL_LAYOUT_PACKED && rows % 64 == 0 && g_opt_orient != 1) {
+    if (h->odd_width) {
+        h->transposed = 1;
+        h->srows = cols;
+        h->swords = rows / 64;
+    } else if (layout == GOL_LAYOUT_PACKED && rows % 64 == 0 && g_opt_orient != 1) {
         bool t = g_opt_orient == 2;
         if (!t) {
             const TuneEntry a = tune_lookup(rows, cols), b = tune_lookup(cols, rows);
@@ -911,9 +923,13 @@ int gol_set(gol_handle h, const uint8_t *cells, size_t n) {
         int32_t *bad = (int32_t *)((char *)st.p + flag_off);
         CU(cudaMemsetAsync(bad, 0, sizeof(int32_t), g_stream));
         CU(cudaMemcpyAsync(st.p, cells, n, cudaMemcpyHostToDevice, g_stream));
-        CU(launch_pack((const uint8_t *)st.p, (uint64_t *)h->buf[1], h->rows, h->words, bad, g_stream));
-        CU(launch_orient((const uint64_t *)h->buf[1], (uint64_t *)h->buf[0], h->rows, h->words, h->transposed, true,
-                         g_stream));
+        if (h->odd_width) {
+            CU(launch_pack_transposed((const uint8_t *)st.p, h->rows, h->cols, (uint64_t *)h->buf[0], bad, g_stream));
+        } else {
+            CU(launch_pack((const uint8_t *)st.p, (uint64_t *)h->buf[1], h->rows, h->words, bad, g_stream));
+            CU(launch_orient((const uint64_t *)h->buf[1], (uint64_t *)h->buf[0], h->rows, h->words, h->transposed,
+                             true, g_stream));
+        }
         int32_t bad_h = 0;
         CU(cudaMemcpyAsync(&bad_h, bad, sizeof bad_h, cudaMemcpyDeviceToHost, g_stream));
         CU(cudaStreamSynchronize(g_stream));
@@ -936,9 +952,14 @@ int gol_get(gol_handle h, uint8_t *cells, size_t n) {
     const size_t woff = (n + 255) & ~size_t(255);
     Scratch st(woff + n / 8);
     if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", n);
-    uint64_t *words = (uint64_t *)((char *)st.p + woff);
-    CU(launch_orient((const uint64_t *)h->buf[h->cur], words, h->rows, h->words, h->transposed, false, g_stream));
-    CU(launch_unpack(words, (uint8_t *)st.p, h->rows, h->words, g_stream));
+    if (h->odd_width) {
+        CU(launch_unpack_transposed((const uint64_t *)h->buf[h->cur], h->rows, h->cols, (uint8_t *)st.p, g_stream));
+    } else {
+        uint64_t *words = (uint64_t *)((char *)st.p + woff);
+        CU(launch_orient((const uint64_t *)h->buf[h->cur], words, h->rows, h->words, h->transposed, false,
+                         g_stream));
+        CU(launch_unpack(words, (uint8_t *)st.p, h->rows, h->words, g_stream));
+    }
     CU(cudaMemcpyAsync(cells, st.p, n, cudaMemcpyDeviceToHost, g_stream));
     return sync_stream();
 }
@@ -947,6 +968,7 @@ int gol_set_packed(gol_handle h, const uint64_t *words, size_t nwords) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!valid(h) || !words) return fail(GOL_EINVAL, "invalid handle or null words");
     if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board is not packed");
+    if (h->odd_width) return fail(GOL_EINVAL, "a board %lld cells wide has no packed word layout", (long long)h->cols);
     if (nwords != (size_t)(h->rows * h->words))
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
     h->cur = 0;
@@ -961,6 +983,7 @@ int gol_get_packed(gol_handle h, uint64_t *words, size_t nwords) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!valid(h) || !words) return fail(GOL_EINVAL, "invalid handle or null words");
     if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board is not packed");
+    if (h->odd_width) return fail(GOL_EINVAL, "a board %lld cells wide has no packed word layout", (long long)h->cols);
     if (nwords != (size_t)(h->rows * h->words))
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
     Scratch st(nwords * 8);
@@ -975,6 +998,7 @@ int gol_set_packed_device(gol_handle h, const uint64_t *dwords, size_t nwords) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!valid(h) || !dwords) return fail(GOL_EINVAL, "invalid handle or null words");
     if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board is not packed");
+    if (h->odd_width) return fail(GOL_EINVAL, "a board %lld cells wide has no packed word layout", (long long)h->cols);
     if (nwords != (size_t)(h->rows * h->words))
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
     h->cur = 0;
@@ -988,6 +1012,7 @@ int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!valid(h) || !dwords) return fail(GOL_EINVAL, "invalid handle or null words");
     if (h->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board is not packed");
+    if (h->odd_width) return fail(GOL_EINVAL, "a board %lld cells wide has no packed word layout", (long long)h->cols);
     if (nwords != (size_t)(h->rows * h->words))
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
     CU(launch_orient((const uint64_t *)h->buf[h->cur], dwords, h->rows, h->words, h->transposed, false, g_stream));
@@ -1031,6 +1056,8 @@ int copy_plan(const gol_handle *hs, size_t n, const CopyPlan **out) {
     for (size_t i = 0; i < n; ++i) {
         if (!valid(hs[i])) return fail(GOL_EINVAL, "invalid handle at %zu", i);
         if (hs[i]->layout != GOL_LAYOUT_PACKED) return fail(GOL_EINVAL, "board %zu is not packed", i);
+        if (hs[i]->odd_width) return fail(GOL_EINVAL, "board %zu is %lld cells wide: no packed word layout", i,
+                                          (long long)hs[i]->cols);
     }
     for (size_t k = 0; k < g_copy_plans.size(); ++k) {
         const CopyPlan &P = *g_copy_plans[k];
@@ -1162,7 +1189,7 @@ int gol_get_region(gol_handle h, int64_t r0, int64_t c0, int64_t nr, int64_t nc,
     Scratch st(n);
     if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", n);
     if (h->layout == GOL_LAYOUT_PACKED)
-        CU(launch_region_packed((const uint64_t *)h->buf[h->cur], h->rows, h->words, r0, c0, nr, nc,
+        CU(launch_region_packed((const uint64_t *)h->buf[h->cur], h->rows, h->cols, r0, c0, nr, nc,
                                 (uint8_t *)st.p, h->transposed != 0, g_stream));
     else
         CU(launch_region_bytes((const uint8_t *)h->buf[h->cur], h->rows, h->cols, r0, c0, nr, nc,
@@ -1199,7 +1226,7 @@ int gol_population_trace(gol_handle h, int64_t every, size_t n, uint64_t *out) {
         int rc = step_batch_locked(&h, &every, 1);
         if (rc) return rc;
         if (h->layout == GOL_LAYOUT_PACKED)
-            CU(launch_popcount_packed((const uint64_t *)h->buf[h->cur], h->rows * h->words, slots + i, g_stream));
+            CU(launch_popcount_packed((const uint64_t *)h->buf[h->cur], h->srows * h->swords, slots + i, g_stream));
         else
             CU(launch_popcount_bytes((const uint8_t *)h->buf[h->cur], h->rows * h->cols, slots + i, g_stream));
     }
@@ -1266,7 +1293,7 @@ int gol_population(gol_handle h, uint64_t *out) {
     if (!st.p) return fail(GOL_ENOMEM, "population scratch");
     CU(cudaMemsetAsync(st.p, 0, sizeof(unsigned long long), g_stream));
     if (h->layout == GOL_LAYOUT_PACKED)
-        CU(launch_popcount_packed((const uint64_t *)h->buf[h->cur], h->rows * h->words,
+        CU(launch_popcount_packed((const uint64_t *)h->buf[h->cur], h->srows * h->swords,
                                   (unsigned long long *)st.p, g_stream));
     else
         CU(launch_popcount_bytes((const uint8_t *)h->buf[h->cur], h->rows * h->cols,

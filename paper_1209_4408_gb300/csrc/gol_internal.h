@@ -176,8 +176,12 @@ cudaError_t launch_pack(const uint8_t *cells, uint64_t *words, int64_t R, int64_
                         cudaStream_t s);
 cudaError_t launch_check_bytes(const uint8_t *cells, int64_t n, int32_t *bad, cudaStream_t s);
 cudaError_t launch_unpack(const uint64_t *words, uint8_t *cells, int64_t R, int64_t W, cudaStream_t s);
-cudaError_t launch_region_packed(const uint64_t *words, int64_t R, int64_t W, int64_t r0, int64_t c0,
-                                 int64_t nr, int64_t nc, uint8_t *out, bool transposed, cudaStream_t s);
+cudaError_t launch_region_packed(const uint64_t *words, int64_t R, int64_t C, int64_t r0, int64_t c0, int64_t nr,
+                                 int64_t nc, uint8_t *out, bool transposed, cudaStream_t s);
+// boards of any width stored transposed (R % 64 == 0), to / from one byte per cell
+cudaError_t launch_pack_transposed(const uint8_t *cells, int64_t R, int64_t C, uint64_t *store, int32_t *bad,
+                                   cudaStream_t s);
+cudaError_t launch_unpack_transposed(const uint64_t *store, int64_t R, int64_t C, uint8_t *cells, cudaStream_t s);
 // R x W interchange words <-> resident storage (the transpose when
 // `transposed`); to_res selects the direction.  src and dst must differ when
 // transposed.

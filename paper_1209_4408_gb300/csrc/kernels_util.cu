@@ -179,10 +179,10 @@ __device__ __forceinline__ int64_t wrap(int64_t x, int64_t m) {
     return r < 0 ? r + m : r;
 }
 
-__global__ void region_packed_kernel(const uint64_t *__restrict__ words, int64_t R, int64_t W,
+__global__ void region_packed_kernel(const uint64_t *__restrict__ words, int64_t R, int64_t C,
                                      int64_t r0, int64_t c0, int64_t nr, int64_t nc,
                                      uint8_t *__restrict__ out, bool transposed) {
-    const int64_t n = nr * nc, C = W * 64;
+    const int64_t n = nr * nc, W = C / 64;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t y = i / nc, x = i - y * nc;
@@ -321,6 +321,42 @@ __global__ void byte_resident_kernel(const uint8_t *__restrict__ in, uint8_t *__
     for (int i = threadIdx.x; i < h * C; i += blockDim.x) {
         const int lr = i / C, c = i - lr * C;
         out[(int64_t)(r0 + lr) * C + c] = (uint8_t)((res[(size_t)lr * W + (c >> 6)] >> (c & 63)) & 1);
+    }
+}
+
+// --- boards stored transposed straight from / to one byte per cell -----------
+// Stored row j holds column j of the R x C board, word i of it rows
+// [64 i, 64 i + 64) (resident layout); R % 64 == 0, C arbitrary.  Neighbouring
+// threads take neighbouring columns, so each of the 64 byte rows a word
+// gathers is read (or written) coalesced.  Bytes other than 0 / 1 set *bad.
+__global__ void pack_transposed_kernel(const uint8_t *__restrict__ cells, int64_t R, int64_t C,
+                                       uint64_t *__restrict__ store, int32_t *bad) {
+    const int64_t sw = R / 64, n = sw * C;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / C, j = idx - i * C;
+        const uint8_t *col = cells + 64 * i * C + j;
+        uint64_t w = 0;
+        bool b = false;
+        for (int k = 0; k < 64; ++k) {
+            const uint8_t v = col[(int64_t)k * C];
+            b |= v > 1;
+            w |= (uint64_t)(v & 1u) << k;
+        }
+        if (b) atomicExch(bad, 1);
+        store[j * sw + i] = to_resident(w);
+    }
+}
+
+__global__ void unpack_transposed_kernel(const uint64_t *__restrict__ store, int64_t R, int64_t C,
+                                         uint8_t *__restrict__ cells) {
+    const int64_t sw = R / 64, n = sw * C;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / C, j = idx - i * C;
+        const uint64_t w = to_interchange(store[j * sw + i]);
+        uint8_t *col = cells + 64 * i * C + j;
+        for (int k = 0; k < 64; ++k) col[(int64_t)k * C] = (uint8_t)((w >> k) & 1u);
     }
 }
 
@@ -517,9 +553,20 @@ cudaError_t launch_unpack(const uint64_t *words, uint8_t *cells, int64_t R, int6
     return cudaGetLastError();
 }
 
-cudaError_t launch_region_packed(const uint64_t *words, int64_t R, int64_t W, int64_t r0, int64_t c0,
+cudaError_t launch_region_packed(const uint64_t *words, int64_t R, int64_t C, int64_t r0, int64_t c0,
                                  int64_t nr, int64_t nc, uint8_t *out, bool transposed, cudaStream_t s) {
-    region_packed_kernel<<<grid_for(nr * nc), kBlock, 0, s>>>(words, R, W, r0, c0, nr, nc, out, transposed);
+    region_packed_kernel<<<grid_for(nr * nc), kBlock, 0, s>>>(words, R, C, r0, c0, nr, nc, out, transposed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_transposed(const uint8_t *cells, int64_t R, int64_t C, uint64_t *store, int32_t *bad,
+                                   cudaStream_t s) {
+    if (R * C > 0) pack_transposed_kernel<<<grid_for((R / 64) * C), kBlock, 0, s>>>(cells, R, C, store, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_transposed(const uint64_t *store, int64_t R, int64_t C, uint8_t *cells, cudaStream_t s) {
+    if (R * C > 0) unpack_transposed_kernel<<<grid_for((R / 64) * C), kBlock, 0, s>>>(store, R, C, cells);
     return cudaGetLastError();
 }
 

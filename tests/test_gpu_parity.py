@@ -293,6 +293,41 @@ def test_batch_repeat_replays_graph(gol):
             gol.gol_set_stream(None)
 
 
+@pytest.mark.parametrize("R,C", [(64, 1), (64, 65), (128, 3), (128, 100), (192, 1000), (640, 333), (1024, 2049)])
+def test_packed_any_width_when_height_is_a_multiple_of_64(gol, opts, R, C):
+    # a width that is not a multiple of 64 is packed, stored transposed
+    # (whole words along the height); every way in and out that has a meaning
+    # for it works, the packed word layout is refused
+    cells = synth.bernoulli_board(R, C, 0.4, 17 * R + C)
+    for torus in (True, False):
+        b = gol.Board(R, C, torus=torus)
+        assert gol.gol_info(b.handle)[3] == gol.GOL_LAYOUT_PACKED
+        b.set(cells)
+        assert_same(b.get(), cells, "round trip %dx%d" % (R, C))
+        x = cells
+        for g, k in ((1, 0), (5, 4), (21, 8)):
+            opts(k, 0)
+            b.step(g)
+            x = oracle.run(x, g, torus)
+            assert_same(b.get(), x, "%dx%d torus=%s after %d" % (R, C, torus, b.generation()))
+        opts(0, 0)
+        assert b.population() == oracle.population(x)
+        reg = b.region(R - 3, C - 2, 7, min(C, 9))
+        assert_same(reg, x[np.ix_(np.arange(R - 3, R + 4) % R, np.arange(C - 2, C - 2 + min(C, 9)) % C)],
+                    "region %dx%d" % (R, C))
+        with pytest.raises(gol.GolError):
+            b.get_packed()
+        b.close()
+    # and in a batch beside other boards
+    other = synth.bernoulli_board(64, 128, 0.4, 5)
+    b1, b2 = gol.Board(R, C), gol.Board(64, 128)
+    b1.set(cells)
+    b2.set(other)
+    gol.step_batch([b1, b2], [9, 4])
+    assert_same(b1.get(), oracle.run(cells, 9), "batched %dx%d" % (R, C))
+    assert_same(b2.get(), oracle.run(other, 4), "batched 64x128")
+
+
 def test_mixed_layouts_and_edges_in_one_batch(gol):
     cases = [(50, 64, True, 0), (50, 64, False, 0), (30, 45, True, 0), (30, 45, False, 0), (70, 2176, False, 0)]
     boards, cells, gens = [], [], []
@@ -345,9 +380,11 @@ def test_torch_allocator_and_stream(gol):
 
 
 def test_invalid_arguments(gol):
+    # packed needs a width or a height that is a multiple of 64
     with pytest.raises(gol.GolError) as e:
-        gol.gol_create_ex(64, 100, True, gol.GOL_LAYOUT_PACKED)
+        gol.gol_create_ex(30, 100, True, gol.GOL_LAYOUT_PACKED)
     assert e.value.code == gol.GOL_EINVAL
+    gol.gol_destroy(gol.gol_create_ex(64, 100, True, gol.GOL_LAYOUT_PACKED))
     b = gol.Board(8, 64)
     bad = np.zeros((8, 64), np.uint8)
     bad[3, 5] = 2
