@@ -184,7 +184,7 @@ const char *gol_last_error(void);
 
 /* Tuning knobs (process wide).  Keys:
  *   GOL_OPT_GENS_PER_PASS  generations per pass over a packed board (1, 2,
- *                          3, 4, 5, 6, 8 or 16; 0 = let the autotune table
+ *                          3, 4, 5, 6, 7, 8 or 16; 0 = let the autotune table
  *                          decide)
  *   GOL_OPT_TILE_ROWS      rows per warp strip of a packed board (>= 1;
  *                          0 = autotune table, shortened for boards with

@@ -236,8 +236,8 @@ struct Plan {
 };
 
 // generations-per-pass values with a kernel instantiation (persist_k*.cu)
-#define GOL_FOR_EACH_K(X) X(1) X(2) X(3) X(4) X(5) X(6) X(8) X(16)
-constexpr int kKs[] = {1, 2, 3, 4, 5, 6, 8, 16};
+#define GOL_FOR_EACH_K(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(16)
+constexpr int kKs[] = {1, 2, 3, 4, 5, 6, 7, 8, 16};
 
 bool is_supported_k(int k) {
     for (int v : kKs)
@@ -1323,7 +1323,7 @@ int gol_set_option(int key, int64_t v) {
     switch (key) {
         case GOL_OPT_GENS_PER_PASS:
             if (!(v == 0 || is_supported_k((int)v)))
-                return fail(GOL_EINVAL, "generations per pass must be 0 or one of 1, 2, 3, 4, 5, 6, 8, 16");
+                return fail(GOL_EINVAL, "generations per pass must be 0 or one of 1, 2, 3, 4, 5, 6, 7, 8, 16");
             g_opt_k = v;
             return GOL_OK;
         case GOL_OPT_TILE_ROWS:

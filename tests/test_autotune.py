@@ -33,7 +33,7 @@ def test_table_save_and_load(mods, tmp_path):
     k, rows = gol.gol_tune_get(64, 64)
     assert k >= 1 and rows >= 1
     with pytest.raises(gol.GolError):
-        gol.gol_tune_set(64, 64, 7, 32)      # no kernel for 7 generations per pass
+        gol.gol_tune_set(64, 64, 9, 32)      # no kernel for 9 generations per pass
     gol.gol_tune_reset()
     assert gol.gol_tune_get(512, 1024) == gol.gol_tune_get(64, 64)
 

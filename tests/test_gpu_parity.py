@@ -166,7 +166,7 @@ def test_packed_random_shapes(gol, opts, R, C, torus):
         gol.gol_set_option(gol.GOL_OPT_PIPELINE, -1)
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 8, 16])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7, 8, 16])
 @pytest.mark.parametrize("rows", [1, 8, 64, 1000])
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_packed_result_independent_of_pass_and_tile(gol, opts, k, rows, variant):
