@@ -19,7 +19,7 @@ import numpy as np
 
 from . import gol
 
-DEFAULT_K = (2, 4, 8, 16)
+DEFAULT_K = (4, 5, 6, 7, 8)
 DEFAULT_ROWS = (8, 16, 32, 64, 128, 256)
 
 
