@@ -1118,7 +1118,7 @@ namespace {
 // other pointer (pageable memory goes through a staging buffer).  In place
 // pays for transfers without boards stored transposed: a 32 MiB board moves
 // in 0.18 / 0.21 ms up / down in place against 0.20 / 0.24 ms staged, a
-// 2 GiB board in 19.5 / 19.1 ms against 51.6 / 81.2 ms.  Tile transposes
+// 2 GiB board in 10–20 ms each way (two runs) against 51.6 / 81.2 ms.  Tile transposes
 // read and write 64-byte pieces of rows, which the copy engine plus a
 // device-side pass moves faster (4096-board batch: 0.76 / 0.84 ms staged
 // against 0.80 / 0.98 ms in place).
