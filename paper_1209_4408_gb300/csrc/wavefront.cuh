@@ -32,12 +32,14 @@
 // Scheduling.  A unit's pass p reads pass p-1 output of every unit whose
 // output its halo touches (its neighbours) and overwrites the buffer those
 // units read during pass p-1; it may start once all of them have completed
-// pass p-1.  Warps take work from a global queue (tickets on head, slots
-// filled in order); after a pass a warp adds one to the join counter of u and
-// of each neighbour (complete_pass): the finisher that completes a counter
-// claims that unit and either runs it next in the same warp or appends it to
-// the queue.  Every wait is bounded: a waiter gives up after `timeout_ns`
-// without any task completing, records GOL_ETIMEOUT and returns.
+// pass p-1.  After a pass a warp counts down the join counter of u and of
+// each neighbour (complete_pass): the finisher that empties a counter claims
+// that unit and either runs it next in the same warp or queues it.  Queued
+// passes wait in two rings, critical (much of the unit's chain still ahead)
+// and the rest; warps take slots by atomicAdd tickets only and serve the
+// critical ring first (take_work).  Every wait is bounded: a waiter gives up
+// after `timeout_ns` without any task completing, records GOL_ETIMEOUT and
+// returns.
 #pragma once
 
 #include <type_traits>
