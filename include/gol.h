@@ -254,6 +254,36 @@ int gol_tune_get(int64_t rows, int64_t cols, int *gens_per_pass, int *tile_rows)
 /* Removes every entry of the autotune table (built-in defaults apply). */
 int gol_tune_reset(void);
 
+/* Unit plan of a packed step (host only, no device needed).  Describes the
+ * units a persistent launch uses for one board stored as `rows` x `words`
+ * resident words per row (a board of cols % 64 == 0 is stored rows x
+ * cols/64; one stored transposed is stored cols x rows/64), with
+ * `gens_per_pass` generations per pass (a supported value, see
+ * gol_tune_set) and `tile_rows` rows per unit (before any chain cap a batch
+ * launch applies).  A unit is the rectangle of output cells one warp
+ * produces per pass: the spatial blocking of Section 2.2 with the temporal
+ * halo of K rows and one word.  *count receives the number of units; when
+ * `out` is not NULL it must hold `cap` >= *count records of
+ * GOL_UNIT_FIELDS int32 each:
+ *   [0] r0, [1] r_end   output rows [r0, r_end) of the unit's row block
+ *   [2] H               rows per segment
+ *   [3] S               segments: full-row units split their row block into
+ *                       S segments of H rows (the last one clipped), tiled
+ *                       units have S = 1
+ *   [4] w0, [5] U       output words [w0, w0 + U)
+ *   [6] mode            0 = full rows (words <= 32), 1 = word tile
+ *   [7] nnb             neighbour units (<= 8): those whose output the
+ *                       unit's halo reads, which are also those that read
+ *                       the unit's output
+ *   [8 .. 15]           neighbour unit indices, -1 past nnb
+ *   [16] cost           row iterations of a pass of the board's tallest
+ *                       unit, H + 2K
+ * Unit i covers row block i / nt and tile i % nt, where nt is the number of
+ * tiles.  Returns GOL_EINVAL for bad arguments or a short buffer. */
+#define GOL_UNIT_FIELDS 17
+int gol_plan_units(int64_t rows, int64_t words, int gens_per_pass, int tile_rows, int32_t *out, size_t cap,
+                   size_t *count);
+
 /* Device facts used for rooflines: SM count, L2 bytes, SM clock (kHz). */
 int gol_device_info(int *sm_count, int64_t *l2_bytes, int *sm_clock_khz);
 

@@ -1407,6 +1407,30 @@ int gol_tune_get(int64_t rows, int64_t cols, int *k, int *tile_rows) {
     return GOL_OK;
 }
 
+static_assert(GOL_UNIT_FIELDS == 9 + kMaxNeighbours, "unit record layout");
+
+int gol_plan_units(int64_t rows, int64_t words, int k, int tile_rows, int32_t *out, size_t cap, size_t *count) {
+    if (rows < 1 || words < 1 || rows > INT32_MAX || words > INT32_MAX / 64 || !is_supported_k(k) || tile_rows < 1)
+        return fail(GOL_EINVAL, "bad unit plan request");
+    const UnitGrid g = unit_grid(rows, words, k, tile_rows);
+    const size_t n = (size_t)g.nb * g.nt;
+    if (count) *count = n;
+    if (!out) return GOL_OK;
+    if (cap < n) return fail(GOL_EINVAL, "unit plan needs %zu records, buffer holds %zu", n, cap);
+    std::vector<UnitDesc> us(n);
+    fill_units(rows, words, 0, g, us.data(), 0);
+    set_board_cost(us.data(), (int)n, k);
+    for (size_t i = 0; i < n; ++i) {
+        const UnitDesc &u = us[i];
+        int32_t *o = out + i * GOL_UNIT_FIELDS;
+        const int32_t f[8] = {u.r0, u.r_end, u.H, u.S, u.w0, u.U, u.mode, u.nnb};
+        for (int j = 0; j < 8; ++j) o[j] = f[j];
+        for (int j = 0; j < kMaxNeighbours; ++j) o[8 + j] = j < u.nnb ? u.nb[j] : -1;
+        o[8 + kMaxNeighbours] = u.cost;
+    }
+    return GOL_OK;
+}
+
 int gol_device_info(int *sms, int64_t *l2, int *clk) {
     std::lock_guard<std::mutex> lk(g_mu);
     int rc = ensure_device();

@@ -53,7 +53,7 @@ EXPORTED = (
     "gol_sync",
     "gol_set_stream", "gol_set_allocator", "gol_last_error", "gol_set_option", "gol_get_option",
     "gol_tune_set", "gol_tune_get", "gol_tune_reset", "gol_device_info", "gol_probe_int_throughput",
-    "gol_debug_unfilled_wait", "gol_step_packed_noalloc",
+    "gol_debug_unfilled_wait", "gol_step_packed_noalloc", "gol_plan_units",
 )
 
 
@@ -111,6 +111,7 @@ def load() -> ctypes.CDLL:
         "gol_probe_int_throughput": [P(ctypes.c_double), P(ctypes.c_double)],
         "gol_debug_unfilled_wait": [i64],
         "gol_step_packed_noalloc": [vp, vp, i64, i64, i32, i64, vp],
+        "gol_plan_units": [i64, i64, i32, i32, P(i32), ctypes.c_size_t, P(ctypes.c_size_t)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -343,6 +344,29 @@ def gol_tune_get(rows: int, cols: int):
 
 def gol_tune_reset():
     _check(load().gol_tune_reset())
+
+
+UNIT_FIELDS = 17
+UNIT_FIELD_NAMES = ("r0", "r_end", "H", "S", "w0", "U", "mode", "nnb")
+
+
+def gol_plan_units(rows: int, words: int, gens_per_pass: int, tile_rows: int):
+    """Units of a packed step of a board stored as rows x words (host only):
+    a list of dicts with the fields of include/gol.h's unit record, the
+    neighbour indices as ``nb`` and the pass cost as ``cost``."""
+    lib = load()
+    n = ctypes.c_size_t()
+    _check(lib.gol_plan_units(rows, words, gens_per_pass, tile_rows, None, 0, ctypes.byref(n)))
+    buf = (ctypes.c_int32 * (UNIT_FIELDS * max(1, n.value)))()
+    _check(lib.gol_plan_units(rows, words, gens_per_pass, tile_rows, buf, n.value, ctypes.byref(n)))
+    units = []
+    for i in range(n.value):
+        rec = buf[i * UNIT_FIELDS:(i + 1) * UNIT_FIELDS]
+        u = dict(zip(UNIT_FIELD_NAMES, rec[:8]))
+        u["nb"] = list(rec[8:8 + u["nnb"]])
+        u["cost"] = rec[16]
+        units.append(u)
+    return units
 
 
 def gol_device_info():
