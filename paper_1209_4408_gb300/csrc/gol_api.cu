@@ -29,6 +29,7 @@ struct gol_board {
     void (*free_fn)(void *, void *) = nullptr;
     void *alloc_ctx = nullptr;
     uint64_t serial = 0;                     // identity for the plan cache
+    uint64_t batch_stamp = 0;                // last batch call that listed the board (repeat check)
     // Packed boards may be stored transposed (stored row c holds column c of
     // the board): the step is symmetric under transposition, and a board
     // whose columns fit the warp lanes better that way runs faster.  The
@@ -172,6 +173,7 @@ int sync_stream() {
 }
 
 bool valid(gol_handle h) { return h != nullptr && h->rows > 0; }
+uint64_t g_batch_stamp = 0;   // gol_step_batch calls so far (under g_mu)
 
 // ---------------------------------------------------------------------------
 // autotune table
@@ -1238,11 +1240,13 @@ namespace {
 int step_batch_locked(const gol_handle *hs, const int64_t *generations, size_t n) {
     if (n == 0) return GOL_OK;
     if (!hs || !generations) return fail(GOL_EINVAL, "null arrays");
-    std::unordered_set<gol_handle> seen;
+    // repeated handles: each call stamps the boards it lists (no per-call allocation)
+    const uint64_t stamp = ++g_batch_stamp;
     for (size_t i = 0; i < n; ++i) {
         if (!valid(hs[i])) return fail(GOL_EINVAL, "invalid handle at %zu", i);
         if (generations[i] < 0) return fail(GOL_EINVAL, "negative generation count at %zu", i);
-        if (!seen.insert(hs[i]).second) return fail(GOL_EINVAL, "handle repeated at %zu", i);
+        if (hs[i]->batch_stamp == stamp) return fail(GOL_EINVAL, "handle repeated at %zu", i);
+        hs[i]->batch_stamp = stamp;
     }
     // byte boards one by one
     for (size_t i = 0; i < n; ++i)

@@ -394,6 +394,15 @@ def test_invalid_arguments(gol):
         b.step(-1)
     with pytest.raises(gol.GolError):
         gol.gol_step_batch([b.handle, b.handle], [1, 1])
+    b2 = gol.Board(64, 64)
+    with pytest.raises(gol.GolError):
+        gol.gol_step_batch([b.handle, b2.handle, b.handle], [1, 1, 1])
+    # a rejected call leaves the boards usable in the next batch
+    gol.gol_step_batch([b2.handle, b.handle], [1, 2])
+    gol.gol_step_batch([b.handle, b2.handle], [1, 1])
+    gol.gol_sync(b.handle)
+    assert gol.gol_generation(b.handle) == 3 and gol.gol_generation(b2.handle) == 2
+    b2.close()
     with pytest.raises(gol.GolError):
         gol.gol_set(b.handle, np.zeros(10, np.uint8))
     for rows, cols in [(0, 64), (64, 0), (-1, 5)]:
