@@ -124,7 +124,7 @@ def check_plan(rows, words, k, tile_rows, dense_limit=1 << 22):
 
 @pytest.mark.parametrize("rows,words,k,tile_rows", [
     (16384, 256, 8, 64),      # 16384^2 board, tuned
-    (131072, 2048, 8, 256),   # 131072^2 board, tuned
+    (131072, 2048, 8, 512),   # 131072^2 board, tuned
     (2048, 32, 6, 128),       # widest board of the 4096-board batch
     (32, 1, 6, 128),          # narrowest
     (64, 1, 8, 128), (96, 2, 6, 128), (256, 3, 6, 128),
