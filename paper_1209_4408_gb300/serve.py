@@ -105,11 +105,26 @@ class Server:
         stats.latencies_s.append(now - job.arrival_s)
 
     def run(self, jobs: Sequence[Job]) -> ServeStats:
-        """Serves ``jobs`` (sorted by arrival) against the wall clock."""
+        """Serves ``jobs`` (sorted by arrival) against the wall clock.  If a
+        library call fails, the boards of the admitted requests are freed
+        before the error propagates."""
+        active: list[Job] = []
+        try:
+            return self._run(jobs, active)
+        except BaseException:
+            for j in active:
+                if j.handle is not None:
+                    try:
+                        self.g.gol_destroy(j.handle)
+                    except Exception:
+                        pass
+                    j.handle = None
+            raise
+
+    def _run(self, jobs: Sequence[Job], active: list) -> ServeStats:
         jobs = sorted(jobs, key=lambda j: j.arrival_s)
         stats = ServeStats()
         waiting: list[Job] = []
-        active: list[Job] = []
         used = 0
         nxt = 0
         t0 = self.clock()
@@ -120,9 +135,9 @@ class Server:
                 nxt += 1
             while waiting and used + waiting[0].bytes_on_device <= self.budget:
                 j = waiting.pop(0)
+                active.append(j)
                 self._admit(j, now)
                 used += j.bytes_on_device
-                active.append(j)
             if waiting and not active:
                 raise RuntimeError("request %d needs %d bytes, more than the budget" %
                                    (waiting[0].rid, waiting[0].bytes_on_device))
@@ -156,7 +171,7 @@ class Server:
                     used -= j.bytes_on_device
                 else:
                     still.append(j)
-            active = still
+            active[:] = still
             self._adapt(cells_gens, dt, active)
         stats.makespan_s = self.clock() - t0
         return stats

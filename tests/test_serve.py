@@ -86,6 +86,87 @@ def test_host_logic_rejects_oversized_request(serve_mod):
         srv.run(jobs)
 
 
+class FailingBackend(FakeBackend):
+    """Fails the n-th batch step (as a library error would)."""
+
+    def __init__(self, fail_at):
+        super().__init__()
+        self.fail_at = fail_at
+
+    def gol_step_batch(self, hs, gens):
+        if len(self.batches) + 1 == self.fail_at:
+            raise RuntimeError("step failed")
+        super().gol_step_batch(hs, gens)
+
+
+@pytest.mark.parametrize("fail_at", [1, 3])
+def test_host_logic_frees_boards_when_a_step_fails(serve_mod, fail_at):
+    fake = FailingBackend(fail_at)
+    jobs = make_jobs(serve_mod, 12, rate=1e6, gen_hi=200)
+    srv = serve_mod.Server(budget_bytes=1 << 30, tick_target_s=1e-4, backend=fake)
+    with pytest.raises(RuntimeError, match="step failed"):
+        srv.run(jobs)
+    assert not fake.boards and fake.live_bytes == 0
+    assert all(j.handle is None for j in jobs)
+
+
+class TickClock:
+    """Deterministic clock: each reading advances by `dt`; a batch step
+    advances it by `tick` (the device time of the step)."""
+
+    def __init__(self, dt=1e-5, tick=5e-3):
+        self.t, self.dt, self.tick = 0.0, dt, tick
+        self.first = None
+
+    def __call__(self):
+        self.t += self.dt
+        if self.first is None:
+            self.first = self.t
+        return self.t
+
+
+class ClockedBackend(FakeBackend):
+    """Records, per batch step, its start time and the requests in it."""
+
+    def __init__(self, clock, jobs):
+        super().__init__()
+        self.clock = clock
+        self.rid_of_words = {id(j.words): j.rid for j in jobs}
+        self.rid_of = {}
+        self.ticks = []
+
+    def gol_set_packed(self, h, words):
+        super().gol_set_packed(h, words)
+        self.rid_of[h] = self.rid_of_words[id(words)]
+
+    def gol_step_batch(self, hs, gens):
+        self.ticks.append((self.clock.t - self.clock.first, {self.rid_of[h] for h in hs}))
+        super().gol_step_batch(hs, gens)
+        self.clock.t += self.clock.tick
+
+
+def test_host_logic_admits_arrivals_at_the_next_tick(serve_mod):
+    """Continuous batching on a deterministic clock: a request that arrives
+    while boards are stepping joins the next tick (memory permitting), so it
+    waits at most one tick plus host time; every request gets exactly its
+    generations; ticks hold several requests at once."""
+    clock = TickClock()
+    jobs = make_jobs(serve_mod, 30, rate=400.0, gen_hi=400)       # arrivals over ~75 ms; 5 ms ticks
+    fake = ClockedBackend(clock, jobs)
+    srv = serve_mod.Server(budget_bytes=1 << 40, tick_target_s=5e-3, quantum_min=8, keep_results=True,
+                           clock=clock, backend=fake)
+    st = srv.run(jobs)
+    assert st.summary()["requests"] == len(jobs)
+    assert all(j.result == j.gens for j in jobs) and not fake.boards
+    host = 200 * clock.dt                                           # generous bound on host readings per tick
+    for j in jobs:
+        first = next(t for t, rids in fake.ticks if j.rid in rids)
+        assert j.arrival_s <= first + 1e-12
+        assert first - j.arrival_s <= clock.tick + host, (j.rid, j.arrival_s, first)
+        assert j.arrival_s <= j.admitted_s <= first + 1e-12 and j.done_s >= first
+    assert max(len(rids) for _, rids in fake.ticks) > 1 and st.ticks >= 10
+
+
 @pytest.mark.gpu
 def test_served_results_equal_alone_and_oracle(serve_mod):
     from paper_1209_4408_gb300 import gol
