@@ -39,7 +39,7 @@ extern "C" {
 #define GOL_ENOMEM (-2)   /* device allocation failed (including the allocator hook)          */
 #define GOL_ECUDA (-3)    /* a CUDA call failed (no device, launch error ...)                  */
 #define GOL_ETIMEOUT (-4) /* a bounded device-side wait gave up; the result is not valid       */
-#define GOL_EBUSY (-5)    /* the handle is in use by an unfinished batch                          */
+#define GOL_EBUSY (-5)    /* reserved; not returned: calls are serialised and stream-ordered      */
 
 /* Board storage chosen at creation. */
 #define GOL_LAYOUT_AUTO 0   /* packed when cols % 64 == 0 or rows % 64 == 0, else bytes         */
