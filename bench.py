@@ -94,6 +94,23 @@ def rank_batch(specs, rank: int):
             for s in specs]
 
 
+def workload_specs(workload: str, nboards: int, rank: int = 0):
+    """The boards of a workload and its description, the same for both arms."""
+    if workload == "single":
+        return ([synth.BoardSpec(0, 16384, 16384, 0.5, 10000, synth.SEED_SINGLE_16K)],
+                "single 16384x16384 toroidal packed board, Bernoulli(0.5), 10000 generations")
+    if workload == "huge":
+        return ([synth.BoardSpec(0, 131072, 131072, 0.5, 1000, synth.SEED_HUGE_128K)],
+                "single 131072x131072 toroidal packed board (2 GiB per buffer), Bernoulli(0.5) with a "
+                "cleared 4096-row band holding a 64x64 glider lattice, 1000 generations")
+    if workload == "bytes":
+        return ([synth.BoardSpec(0, 256, 256, 0.3, 1000, synth.SEED_BYTES_256)],
+                "single 256x256 toroidal byte-per-cell board, Bernoulli(0.3), 1000 generations")
+    specs = rank_batch(synth.batch_specs(nboards), rank)
+    return (specs, "batch of %d uneven toroidal packed boards (rows, cols log-uniform [32, 2048] "
+                   "rounded to x64; density U(0.1,0.6); gens log-uniform [100, 5000])" % len(specs))
+
+
 def max_over_ranks(ms: float, dist, device=None) -> float:
     """The slowest rank's time (the job finishes when the last rank does)."""
     if dist is None:
@@ -169,6 +186,19 @@ class ClockSampler:
 # CPU baseline: the oracle on a bounded sample
 # ---------------------------------------------------------------------------
 CPU_SAMPLE_SIDE = 2048   # larger boards are timed on a crop of this side
+CROP_NOTE = "; boards above %d^2 cells timed on their top-left %d x %d corner as a torus" % (
+    CPU_SAMPLE_SIDE, CPU_SAMPLE_SIDE, CPU_SAMPLE_SIDE)
+
+
+def oracle_sample_cells(s):
+    """Cells of board spec ``s`` for timing the oracle: the whole board, or
+    its top-left CPU_SAMPLE_SIDE^2 corner (stepped as a torus of that size;
+    the oracle's time per cell does not depend on the board size) when the
+    board is larger.  Returns (cells, cropped)."""
+    if s.rows * s.cols > CPU_SAMPLE_SIDE * CPU_SAMPLE_SIDE:
+        nr, nc = min(s.rows, CPU_SAMPLE_SIDE), min(s.cols, CPU_SAMPLE_SIDE)
+        return synth.bernoulli_region(s.rows, s.cols, s.density, s.seed, 0, 0, nr, nc), True
+    return synth.bernoulli_board(s.rows, s.cols, s.density, s.seed), False
 
 
 def cpu_oracle_sample(specs, seconds: float, threads: int = 1):
@@ -186,12 +216,8 @@ def cpu_oracle_sample(specs, seconds: float, threads: int = 1):
     used = 0
     cropped = False
     for s in pick:
-        if s.rows * s.cols > CPU_SAMPLE_SIDE * CPU_SAMPLE_SIDE:
-            nr, nc = min(s.rows, CPU_SAMPLE_SIDE), min(s.cols, CPU_SAMPLE_SIDE)
-            cells = synth.bernoulli_region(s.rows, s.cols, s.density, s.seed, 0, 0, nr, nc)
-            cropped = True
-        else:
-            cells = synth.bernoulli_board(s.rows, s.cols, s.density, s.seed)
+        cells, crop = oracle_sample_cells(s)
+        cropped = cropped or crop
         g = min(s.gens, 8)
         t = time.perf_counter()
         if threads == 1:
@@ -204,8 +230,7 @@ def cpu_oracle_sample(specs, seconds: float, threads: int = 1):
             break
     desc = "%d boards of the workload (every %dth), min(gens, 8) generations each" % (len(pick), max(1, len(specs) // 16))
     if cropped:
-        desc += "; boards above %d^2 cells timed on their top-left %d x %d corner as a torus" % (
-            CPU_SAMPLE_SIDE, CPU_SAMPLE_SIDE, CPU_SAMPLE_SIDE)
+        desc += CROP_NOTE
     return done_cells / used / 1e9, threads, desc
 
 
@@ -262,20 +287,7 @@ def run_gpu(args, rank, world, local):
         torch.cuda.synchronize()
 
     # ---- workload -----------------------------------------------------------
-    if args.workload == "batch":
-        specs = rank_batch(synth.batch_specs(args.boards), rank)
-        workload = "batch of %d uneven toroidal packed boards (rows, cols log-uniform [32, 2048] " \
-                   "rounded to x64; density U(0.1,0.6); gens log-uniform [100, 5000])" % len(specs)
-    elif args.workload == "single":
-        specs = [synth.BoardSpec(0, 16384, 16384, 0.5, 10000, synth.SEED_SINGLE_16K)]
-        workload = "single 16384x16384 toroidal packed board, Bernoulli(0.5), 10000 generations"
-    elif args.workload == "huge":
-        specs = [synth.BoardSpec(0, 131072, 131072, 0.5, 1000, synth.SEED_HUGE_128K)]
-        workload = ("single 131072x131072 toroidal packed board (2 GiB per buffer), Bernoulli(0.5) with a "
-                    "cleared 4096-row band holding a 64x64 glider lattice, 1000 generations")
-    else:
-        specs = [synth.BoardSpec(0, 256, 256, 0.3, 1000, synth.SEED_BYTES_256)]
-        workload = "single 256x256 toroidal byte-per-cell board, Bernoulli(0.3), 1000 generations"
+    specs, workload = workload_specs(args.workload, args.boards, rank)
 
     total_cells_gens = sum(s.rows * s.cols * s.gens for s in specs)
     total_words_gens = sum(s.rows * (s.cols // 64) * s.gens for s in specs)
@@ -499,17 +511,17 @@ def run_reference(args, rank, world):
     import oracle
 
     oracle.build()
-    specs = synth.batch_specs(args.boards) if args.workload == "batch" else \
-        [synth.BoardSpec(0, 256, 256, 0.3, 1000, synth.SEED_BYTES_256)]
+    specs, workload = workload_specs(args.workload if args.workload != "decomposition" else "batch", args.boards)
     pick = specs[:: max(1, len(specs) // 8)][:8]
-    boards = [(s, synth.bernoulli_board(s.rows, s.cols, s.density, s.seed)) for s in pick]
+    sampled = [oracle_sample_cells(s) for s in pick]
+    boards = [c for c, _ in sampled]
     gens = 2
 
     def step():
         n = 0
-        for s, c in boards:
+        for c in boards:
             oracle.run(c, gens)
-            n += s.rows * s.cols * gens
+            n += c.size * gens
         return n
 
     for _ in range(args.warmup):
@@ -520,12 +532,15 @@ def run_reference(args, rank, world):
         n += step()
     dt = time.perf_counter() - t0
     v = n / dt / 1e9
-    desc = "%d boards taken evenly from the batch, %d generations each per step" % (len(pick), gens)
+    desc = "%d boards taken evenly from the workload, %d generations each per step" % (len(pick), gens)
+    if any(crop for _, crop in sampled):
+        desc += CROP_NOTE
     out = {"impl": "reference", "metric": "GCUPS batched (gol_step_batch) vs plain per-board loop on 1 GB300",
            "value": round(v, 6), "unit": "GCUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded SplitMix64 Bernoulli boards)",
-           "config": {"workload": "oracle (serial, one byte per cell) on a bounded sample of the batch"},
+           "config": {"workload": workload, "boards": len(specs),
+                      "parallelism": "oracle (serial, one byte per cell) on one host core, bounded sample"},
            "cpu_baseline": {"value": round(v, 6), "unit": "GCUPS", "cores": 1, "kind": "oracle", "sample": desc},
            "e2e": {"value": round(v, 6), "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
