@@ -399,6 +399,30 @@ def test_batch_specs_shapes():
     assert len({s.seed for s in specs}) == len(specs)        # distinct board seeds
 
 
+def test_request_stream_recipe():
+    """Poisson arrivals (exponential gaps of mean 1/rate), sides multiples of
+    64 in [64, 8192], densities in [0.1, 0.6], generations in [10, 1e5]."""
+    n, rate = 4000, 650.0
+    reqs = synth.request_stream(n, rate)
+    t = np.array([r.arrival_s for r in reqs])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert (gaps > 0).all()
+    # the mean of n exponential gaps is within 5 standard errors of 1/rate
+    assert abs(gaps.mean() - 1 / rate) < 5 * (1 / rate) / np.sqrt(n)
+    # exponential: the gaps' standard deviation equals their mean
+    assert abs(gaps.std() / gaps.mean() - 1) < 0.1
+    sides = np.array([(r.rows, r.cols) for r in reqs])
+    assert (sides % 64 == 0).all() and sides.min() >= 64 and sides.max() <= 8192
+    d = np.array([r.density for r in reqs])
+    assert d.min() >= 0.1 and d.max() <= 0.6
+    g = np.array([r.gens for r in reqs])
+    assert g.min() >= 10 and g.max() <= 100000
+    # log-uniform generations: the median is near the geometric mean of the range
+    assert abs(np.log(np.median(g)) - 0.5 * (np.log(10) + np.log(1e5))) < 0.3
+    assert synth.request_stream(n, rate)[123] == reqs[123]      # deterministic
+    assert len({r.seed for r in reqs}) == n                     # distinct board seeds
+
+
 def test_glider_band_lattice():
     band = synth.GliderBand(b0=64, band_rows=512, n=4, spacing=16, off_r=100, off_c=64)
     w = synth.glider_band_words(1024, 4, 5, band)
