@@ -20,7 +20,7 @@ import numpy as np
 from . import gol
 
 DEFAULT_K = (4, 5, 6, 7, 8)
-DEFAULT_ROWS = (8, 16, 32, 64, 128, 256)
+DEFAULT_ROWS = (8, 16, 32, 64, 128, 256, 512)
 
 
 SHIPPED_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_gb300.json")
