@@ -149,3 +149,173 @@ def test_a_wrong_lut_is_caught():
             total += 1
             caught += any(run_rule32(mutated, *args) != want for args, want in cases)
     assert caught >= 0.9 * total, (caught, total)
+
+
+# ---------------------------------------------------------------------------
+# Row sums of the packed kernel (even/odd split words, funnel shifts, lane
+# shuffles), read from each pass variant of wavefront.cuh.
+# ---------------------------------------------------------------------------
+M32 = 0xFFFFFFFF
+
+
+def lop3_words(lut, a, b, c):
+    """lop3.b32 on numpy uint32 arrays (the sum of the LUT's minterms)."""
+    import numpy as np
+
+    out = np.zeros_like(a)
+    for idx in range(8):
+        if (lut >> idx) & 1:
+            out |= (a if idx & 4 else ~a) & (b if idx & 2 else ~b) & (c if idx & 1 else ~c)
+    return out
+
+
+def funnelshift(kind, lo, hi, n):
+    """CUDA __funnelshift_l / __funnelshift_r: the high (l) or low (r) 32 bits
+    of the 64-bit value hi:lo shifted left / right by n & 31."""
+    import numpy as np
+
+    v = (hi.astype(np.uint64) << np.uint64(32)) | lo.astype(np.uint64)
+    n = np.uint64(n & 31)
+    if kind == "l":
+        return ((v << n) >> np.uint64(32)).astype(np.uint32)
+    return (v >> n).astype(np.uint32)
+
+
+def braced(text, start):
+    """The text inside the first {...} block at or after `start`."""
+    i = text.index("{", start)
+    depth = 0
+    for j in range(i, len(text)):
+        depth += {"{": 1, "}": -1}.get(text[j], 0)
+        if depth == 0:
+            return text[i + 1:j]
+    raise AssertionError("unbalanced braces")
+
+
+def iterate_bodies():
+    """Bodies of the `iterate` lambdas (one per pass variant)."""
+    text = source("wavefront.cuh")
+    return [braced(text, m.end()) for m in re.finditer(r"auto iterate = \[&\]\([^)]*\)", text)]
+
+
+def row_sum_program(body):
+    consts = lut_constants(source("wavefront.cuh"))
+    shifts = {m.group(1): (m.group(2), m.group(3), m.group(4), int(m.group(5)))
+              for m in re.finditer(r"(\w+) = __funnelshift_([lr])\((\w+),\s*(\w+),\s*(\d+)\)", body)}
+    planes = []
+    for m in re.finditer(r"(\w+)(?:\[\w+\])*\s*=\s*lop3<(\w+)>\((\w+),\s*(\w+),\s*(\w+)\)", body):
+        name, lut, a, b, c = m.groups()
+        pm = re.fullmatch(r"[a-z]([01])([lh])", name)
+        assert pm, name
+        planes.append((int(pm.group(1)), pm.group(2), consts.get(lut, None) or int(lut, 0), a, b, c))
+    return shifts, planes
+
+
+def to_halves(cells_row):
+    """A row of 64 W cells in the resident layout: per word, the low half
+    holds the even columns (bit j = column 2j), the high half the odd ones."""
+    import numpy as np
+
+    w = cells_row.reshape(-1, 64).astype(np.uint64)
+    j = np.arange(32, dtype=np.uint64)
+    lo = (w[:, 0::2] << j).sum(axis=1).astype(np.uint32)
+    hi = (w[:, 1::2] << j).sum(axis=1).astype(np.uint32)
+    return lo, hi
+
+
+def from_halves(lo, hi):
+    import numpy as np
+
+    j = np.arange(32, dtype=np.uint32)
+    cells = np.zeros((lo.size, 64), np.uint8)
+    cells[:, 0::2] = (lo[:, None] >> j) & 1
+    cells[:, 1::2] = (hi[:, None] >> j) & 1
+    return cells.reshape(-1)
+
+
+def kernel_planes(shifts, planes, lo, hi):
+    """Row-sum planes of one row of a torus held as one segment of W lanes:
+    lane k holds word k; the west / east lanes are k -+ 1 mod W."""
+    import numpy as np
+
+    env = {"xl": lo, "xh": hi, "wh": np.roll(hi, 1), "el": np.roll(lo, -1)}
+    for dst, (kind, a, b, n) in shifts.items():
+        env[dst] = funnelshift(kind, env[a], env[b], n)
+    out = {}
+    for plane, half, lut, a, b, c in planes:
+        out[(plane, half)] = lop3_words(lut, env[a], env[b], env[c])
+    return out
+
+
+def test_row_sums_of_every_pass_variant():
+    import numpy as np
+
+    bodies = iterate_bodies()
+    assert len(bodies) == 3                      # register moves, renaming, skewed stages
+    rng = np.random.default_rng(44)
+    for body in bodies:
+        shifts, planes = row_sum_program(body)
+        assert sorted((p, h) for p, h, *_ in planes) == [(0, "h"), (0, "l"), (1, "h"), (1, "l")]
+        for W in (1, 2, 3, 5):
+            row = (rng.random(64 * W) < 0.5).astype(np.uint8)
+            got = kernel_planes(shifts, planes, *to_halves(row))
+            hsum = np.roll(row, 1) + row + np.roll(row, -1)          # west + cell + east on the torus
+            for plane in (0, 1):
+                want = (hsum >> plane) & 1
+                assert np.array_equal(from_halves(got[(plane, "l")], got[(plane, "h")]), want), (plane, W)
+
+
+def test_rule_call_takes_the_middle_row_alive_word():
+    """rule32(t0, t1, m0, m1, b0, b1, alive): the alive word comes from the
+    same window slot as the middle row's planes, the three rows' planes from
+    three different slots, and each call reads one half only."""
+    for body in iterate_bodies():
+        calls = re.findall(r"rule32\(([^;]*)\)\s*;", body)
+        assert len(calls) == 2, calls
+        for call in calls:
+            args = [a.strip() for a in call.split(",")]
+            assert len(args) == 7
+
+            def slot(x):
+                return (x[0], x[x.index("["):] if "[" in x else "")
+
+            assert slot(args[0]) == slot(args[1]) and slot(args[4]) == slot(args[5])
+            assert slot(args[2]) == slot(args[3]) == slot(args[6])
+            assert len({slot(args[0]), slot(args[2]), slot(args[4])}) == 3
+            halves = {a.split("[")[0][-1] for a in args}
+            assert len(halves) == 1 and halves <= {"l", "h"}, args
+
+
+def test_one_generation_from_the_kernel_source_matches_the_oracle():
+    """Row sums (parsed) + rule32 (parsed), composed over rows above, at and
+    below on a torus, equal the oracle's generation."""
+    import numpy as np
+
+    oracle = __import__("pytest").importorskip("oracle")
+    steps = rule32_program()
+    shifts, planes = row_sum_program(iterate_bodies()[1])
+    rng = np.random.default_rng(45)
+
+    def rule_words(t, m, b, alive):
+        out = np.zeros_like(alive)
+        for bit in range(32):
+            sel = np.uint32(1 << bit)
+            for i in range(alive.size):
+                args = [int((x[i] & sel) != 0) for x in (t[0], t[1], m[0], m[1], b[0], b[1], alive)]
+                if run_rule32(steps, *args):
+                    out[i] |= sel
+        return out
+
+    for R, W in ((3, 1), (5, 2), (4, 3)):
+        cells = (rng.random((R, 64 * W)) < 0.4).astype(np.uint8)
+        halves = [to_halves(cells[r]) for r in range(R)]
+        pl = [kernel_planes(shifts, planes, lo, hi) for lo, hi in halves]
+        nxt = np.zeros_like(cells)
+        for r in range(R):
+            above, mid, below = pl[(r - 1) % R], pl[r], pl[(r + 1) % R]
+            lo = rule_words((above[(0, "l")], above[(1, "l")]), (mid[(0, "l")], mid[(1, "l")]),
+                            (below[(0, "l")], below[(1, "l")]), halves[r][0])
+            hi = rule_words((above[(0, "h")], above[(1, "h")]), (mid[(0, "h")], mid[(1, "h")]),
+                            (below[(0, "h")], below[(1, "h")]), halves[r][1])
+            nxt[r] = from_halves(lo, hi)
+        assert np.array_equal(nxt, oracle.run(cells, 1)), (R, W)
