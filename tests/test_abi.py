@@ -73,3 +73,54 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(gol, "LIB_PATH", str(tmp_path / "libgol.so"))
     with pytest.raises(ImportError):
         gol.load()
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <stdlib.h>
+#include "gol.h"
+
+int main(void) {
+    gol_handle h = NULL;
+    int rc = gol_create(64, 128, 1, &h);
+    printf("create %d %s\n", rc, gol_last_error() ? "msg" : "nomsg");
+    size_t n = 0;
+    rc = gol_plan_units(16384, 256, 8, 64, NULL, 0, &n);
+    int32_t *u = (int32_t *)malloc(n * GOL_UNIT_FIELDS * sizeof(int32_t));
+    rc |= gol_plan_units(16384, 256, 8, 64, u, n, &n);
+    printf("plan %d %zu %d %d %d\n", rc, n, u[0], u[1], u[5]);
+    free(u);
+    int k = 0, rows = 0;
+    rc = gol_tune_get(1024, 1024, &k, &rows);
+    printf("tune %d %d %d\n", rc, k > 0, rows > 0);
+    printf("einval %d\n", gol_step(NULL, 1) == GOL_EINVAL);
+    return 0;
+}
+"""
+
+
+def test_c_program_links_and_calls_the_abi(lib, tmp_path):
+    """The header compiles as strict C99 and a C program links the library
+    and calls it: host-only calls answer, device calls refuse without a GPU."""
+    import shutil
+    import subprocess
+
+    from paper_1209_4408_gb300 import gol
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_gol.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "use_gol"
+    libdir = os.path.dirname(gol.LIB_PATH)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-lgol", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        assert out[0] == "create %d msg" % gol.GOL_ECUDA
+    # 256 row blocks x 9 tiles; unit 0 covers rows [0, 64) and words [0, 28)
+    assert out[1] == "plan 0 2304 0 64 28"
+    assert out[2] == "tune 0 1 1"
+    assert out[3] == "einval 1"
