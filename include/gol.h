@@ -279,7 +279,8 @@ int gol_tune_reset(void);
  *   [16] cost           row iterations of a pass of the board's tallest
  *                       unit, H + 2K
  * Unit i covers row block i / nt and tile i % nt, where nt is the number of
- * tiles.  Returns GOL_EINVAL for bad arguments or a short buffer. */
+ * tiles.  Returns GOL_EINVAL for bad arguments, a plan of more than
+ * INT32_MAX units, or a short buffer. */
 #define GOL_UNIT_FIELDS 17
 int gol_plan_units(int64_t rows, int64_t words, int gens_per_pass, int tile_rows, int32_t *out, size_t cap,
                    size_t *count);

@@ -1418,6 +1418,7 @@ int gol_plan_units(int64_t rows, int64_t words, int k, int tile_rows, int32_t *o
         return fail(GOL_EINVAL, "bad unit plan request");
     const UnitGrid g = unit_grid(rows, words, k, tile_rows);
     const size_t n = (size_t)g.nb * g.nt;
+    if (n > (size_t)INT32_MAX) return fail(GOL_EINVAL, "unit plan of %zu units exceeds int32 unit ids", n);
     if (count) *count = n;
     if (!out) return GOL_OK;
     if (cap < n) return fail(GOL_EINVAL, "unit plan needs %zu records, buffer holds %zu", n, cap);

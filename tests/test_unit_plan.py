@@ -160,7 +160,8 @@ def test_ragged_tile_edges(lib):
 
 
 def test_plan_rejects_bad_arguments(lib):
-    for args in ((0, 4, 6, 64), (4, 0, 6, 64), (4, 4, 9, 64), (4, 4, 6, 0), (4, 4, 0, 64)):
+    for args in ((0, 4, 6, 64), (4, 0, 6, 64), (4, 4, 9, 64), (4, 4, 6, 0), (4, 4, 0, 64),
+                 ((1 << 31) - 1, (1 << 25) - 1, 1, 1)):          # more units than int32 ids
         with pytest.raises(gol.GolError):
             gol.gol_plan_units(*args)
     # a short buffer is an error, a NULL buffer only counts
