@@ -302,6 +302,25 @@ def test_decompositions_equal_serial(torus):
         assert np.array_equal(oracle.run_blocks_omp(b, 9, m, n, torus=torus), ref)
 
 
+def test_r_pentomino_stabilises_at_1103_with_116_cells():
+    """A known property of B3/S23, independent of the paper: the R-pentomino
+    is a methuselah whose population settles at generation 1103 at 116 cells
+    (still lifes, blinkers and six escaping gliders), 118 the generation
+    before.  On a 768 x 768 torus nothing wraps into the debris by then."""
+    import os
+
+    N = 768
+    b = np.zeros((N, N), np.uint8)
+    for dr, dc in [(0, 1), (0, 2), (1, 0), (1, 1), (2, 1)]:       # .XX / XX. / .X.
+        b[N // 2 + dr, N // 2 + dc] = 1
+    threads = max(1, os.cpu_count() or 1)
+    x = oracle.run_rows_omp(b, 1102, threads)
+    assert int(x.sum()) == 118
+    for _ in range(3):                                              # generations 1103 .. 1105
+        x = oracle.run_rows_omp(x, 1, threads)
+        assert int(x.sum()) == 116
+
+
 def test_light_cone():
     # cell (r, c) after t generations depends only on initial cells within
     # Chebyshev distance t: a T x T tile equals the centre of the run on the
