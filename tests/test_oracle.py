@@ -321,6 +321,33 @@ def test_r_pentomino_stabilises_at_1103_with_116_cells():
         assert int(x.sum()) == 116
 
 
+def _place_rows(N, rows, r0, c0):
+    b = np.zeros((N, N), np.uint8)
+    for r, line in enumerate(rows):
+        for c, ch in enumerate(line):
+            b[r0 + r, c0 + c] = ch == "O"
+    return b
+
+
+def test_diehard_vanishes_at_generation_130():
+    """Known property of B3/S23: the seven-cell Diehard dies out after
+    exactly 130 generations."""
+    x = _place_rows(128, ["......O.", "OO......", ".O...OOO"], 60, 60)
+    x = oracle.run(x, 129)
+    assert int(x.sum()) > 0
+    assert int(oracle.run(x, 1).sum()) == 0
+
+
+def test_lightweight_spaceship_moves_two_cells_per_four_generations():
+    """Known property of B3/S23: the lightweight spaceship (period 4, nine
+    cells) travels at c/2; on an N-wide torus it is home after 2N
+    generations."""
+    N = 40
+    b = _place_rows(N, [".O..O", "O....", "O...O", "OOOO."], 18, 20)
+    assert np.array_equal(oracle.run(b, 4), np.roll(b, -2, axis=1))
+    assert np.array_equal(oracle.run(b, 2 * N), b)
+
+
 def test_light_cone():
     # cell (r, c) after t generations depends only on initial cells within
     # Chebyshev distance t: a T x T tile equals the centre of the run on the
