@@ -10,10 +10,12 @@ end-to-end figure through host buffers, the roofline of the dominant
 kernel, the oracle's CPU throughput and the SM clocks seen while timing.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload batch|single|bytes]
+                    [--workload batch|single|huge|bytes|decomposition]
 
 ``--impl reference`` times the oracle (the plain serial CPU program of
-``oracle/``) on a bounded sample of the same workload.
+``oracle/``) on a bounded sample of the same workload (boards above 2048^2
+cells on a 2048^2 corner) and prints the same metric for the same
+``config.workload``.
 """
 from __future__ import annotations
 
