@@ -63,8 +63,11 @@ int gol_create(int64_t rows, int64_t cols, int torus, gol_handle *out);
  * GOL_EINVAL for it, gol_set / gol_get / gol_get_region work. */
 int gol_create_ex(int64_t rows, int64_t cols, int torus, int layout, gol_handle *out);
 
-/* Frees the board's device memory after its stream's work has finished.
- * A null handle is GOL_EINVAL. */
+/* Releases the board.  The handle is invalid on return; the device memory
+ * is freed once the work queued on the library's stream before this call
+ * has finished (an event recorded here is polled by later calls, and
+ * gol_set_allocator waits for all of them), so the call does not wait for
+ * the device.  A null handle is GOL_EINVAL. */
 int gol_destroy(gol_handle h);
 
 /* Initial configuration (Section 1: "creating an initial configuration").
@@ -130,7 +133,10 @@ int gol_get_region(gol_handle h, int64_t r0, int64_t c0, int64_t nr, int64_t nc,
  * GPU would race: the library serialises its calls and each call waits for
  * its stream before returning.  Returns GOL_EINVAL for bad arguments or a
  * board too wide for the workspace, GOL_ETIMEOUT if a bounded device wait
- * gave up, GOL_ECUDA for CUDA errors. */
+ * gave up, GOL_ECUDA for CUDA errors.  GOL_EINVAL leaves both buffers
+ * untouched; after GOL_ETIMEOUT or GOL_ECUDA the contents of d_board and
+ * d_spare are unspecified (the board may be left in the library's internal
+ * word order, or its live state in d_spare). */
 int gol_step_packed_noalloc(uint64_t *d_board, uint64_t *d_spare, int64_t rows, int64_t cols, int torus,
                             int64_t generations, void *stream);
 
@@ -284,6 +290,11 @@ int gol_tune_reset(void);
 #define GOL_UNIT_FIELDS 17
 int gol_plan_units(int64_t rows, int64_t words, int gens_per_pass, int tile_rows, int32_t *out, size_t cap,
                    size_t *count);
+
+/* Number of kernels the library has launched in this process (host side
+ * count: each launch adds one, each replay of a graph the library captured
+ * adds the graph's kernels). */
+int gol_kernel_launches(uint64_t *out);
 
 /* Device facts used for rooflines: SM count, L2 bytes, SM clock (kHz). */
 int gol_device_info(int *sm_count, int64_t *l2_bytes, int *sm_clock_khz);

@@ -116,6 +116,16 @@ def test_batch_4096(gol):
         used += cost
         checked += 1
     assert checked >= 256
+    # a seeded random sample of the large boards (both sides >= 1024: several
+    # row blocks, multi-unit plans, the chain cap and the critical ring all at
+    # work) against the oracle at their full generation counts
+    big = [i for i, s in enumerate(specs) if s.rows >= 1024 and s.cols >= 1024]
+    assert len(big) >= 100
+    pick = [big[j] for j in np.random.default_rng(12345).permutation(len(big))[:8]]
+    for i in pick:
+        want = oracle.run_rows_omp(oracle.unpack_words(words[i]), specs[i].gens, THREADS)
+        assert np.array_equal(oracle.unpack_words(boards[i].get_packed()), want), \
+            "large board %d (%d x %d, %d generations)" % (i, specs[i].rows, specs[i].cols, specs[i].gens)
     # the most expensive boards: batch result equals the board stepped alone
     for i in order[-6:]:
         s = specs[i]
