@@ -608,10 +608,43 @@ void reap(bool all) {
     }
 }
 
+// Boards destroyed while work queued before gol_destroy may still use them:
+// their memory is freed once an event recorded at destruction has completed
+// (never from a static destructor, like the plans).
+struct BoardGrave {
+    void *mem[3];
+    void (*free_fn)(void *, void *);
+    void *alloc_ctx;
+    cudaGraphExec_t graphs[2];
+    cudaEvent_t ev;
+};
+std::vector<BoardGrave> &g_board_graves = *new std::vector<BoardGrave>();
+
+void free_board_memory(BoardGrave &g) {
+    for (auto ge : g.graphs)
+        if (ge) cudaGraphExecDestroy(ge);
+    for (void *p : g.mem) dev_free(p, g.free_fn, g.alloc_ctx);
+}
+
+void reap_boards(bool all) {
+    for (size_t i = 0; i < g_board_graves.size();) {
+        if (all) cudaEventSynchronize(g_board_graves[i].ev);
+        if (cudaEventQuery(g_board_graves[i].ev) == cudaSuccess) {
+            free_board_memory(g_board_graves[i]);
+            cudaEventDestroy(g_board_graves[i].ev);
+            g_board_graves.erase(g_board_graves.begin() + i);
+        } else {
+            cudaGetLastError();
+            ++i;
+        }
+    }
+}
+
 void clear_plans() {
     for (auto &p : g_plans) bury(std::move(p));
     g_plans.clear();
     reap(true);
+    reap_boards(true);
 }
 
 Plan *find_plan(const std::vector<gol_handle> &hs, const std::vector<int64_t> &gens, bool torus) {
@@ -679,7 +712,9 @@ int run_packed(const std::vector<gol_handle> &hs, const std::vector<int64_t> &ge
             }
             cudaGraph_t graph = nullptr;
             CU(cudaStreamBeginCapture(g_stream, cudaStreamCaptureModeThreadLocal));
+            set_capturing(true);
             e = launch_plan_kernels(*P, g_stream);
+            set_capturing(false);
             cudaError_t e2 = cudaStreamEndCapture(g_stream, &graph);
             if (e == cudaSuccess && e2 == cudaSuccess) {
                 e = cudaGraphInstantiate(&P->graph, graph, 0);
@@ -698,6 +733,7 @@ int run_packed(const std::vector<gol_handle> &hs, const std::vector<int64_t> &ge
     if (P->graph && !P->no_graph && g_opt_graphs && g_stream != nullptr && P->graph_stream == g_stream) {
         e = cudaGraphLaunch(P->graph, g_stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        count_launches(2);   // the scheduler initialisation and the step kernel
     } else {
         e = launch_plan_kernels(*P, g_stream);
         if (e != cudaSuccess) return cuda_fail(e, "launching the step");
@@ -746,11 +782,13 @@ int step_bytes(gol_handle h, int64_t G) {
             cudaGraph_t graph = nullptr;
             CU(cudaStreamBeginCapture(g_stream, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaSuccess;
+            set_capturing(true);
             for (int g = 0; g < kByteGraphGens && e == cudaSuccess; ++g) {
                 const int c = h->cur ^ (g & 1);
                 e = launch_byte_step((const uint8_t *)h->buf[c], (uint8_t *)h->buf[c ^ 1], h->rows, h->cols,
                                      h->torus, g_stream);
             }
+            set_capturing(false);
             cudaError_t e2 = cudaStreamEndCapture(g_stream, &graph);
             if (e != cudaSuccess) return cuda_fail(e, "capturing byte steps");
             if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
@@ -760,6 +798,7 @@ int step_bytes(gol_handle h, int64_t G) {
         }
         for (; G >= kByteGraphGens; G -= kByteGraphGens) {
             CU(cudaGraphLaunch(ge, g_stream));
+            count_launches(kByteGraphGens);
             h->generation += kByteGraphGens;
         }
     }
@@ -823,6 +862,7 @@ int gol_create_ex(int64_t rows, int64_t cols, int torus, int layout, gol_handle 
         return fail(GOL_EINVAL, "board too large");
     int rc = ensure_device();
     if (rc) return rc;
+    reap_boards(false);
     auto h = new gol_board();
     h->rows = rows;
     h->cols = cols;
@@ -887,14 +927,21 @@ int gol_destroy(gol_handle h) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!valid(h)) return fail(GOL_EINVAL, "invalid handle");
     drop_plans_of(h);
-    cudaStreamSynchronize(g_stream);
-    for (auto ge : h->byte_graph)
-        if (ge) cudaGraphExecDestroy(ge);
-    dev_free(h->buf[0], h->free_fn, h->alloc_ctx);
-    dev_free(h->buf[1], h->free_fn, h->alloc_ctx);
-    dev_free(h->dev_cur, h->free_fn, h->alloc_ctx);
+    reap_boards(false);
+    BoardGrave g{{h->buf[0], h->buf[1], h->dev_cur}, h->free_fn, h->alloc_ctx,
+                 {h->byte_graph[0], h->byte_graph[1]}, nullptr};
     h->rows = 0;
     delete h;
+    // the memory is freed once the work queued so far on the stream has run
+    if (cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(g.ev, g_stream) != cudaSuccess) {
+        cudaGetLastError();
+        if (g.ev) cudaEventDestroy(g.ev);
+        cudaStreamSynchronize(g_stream);
+        free_board_memory(g);
+        return GOL_OK;
+    }
+    g_board_graves.push_back(g);
     return GOL_OK;
 }
 
@@ -1433,6 +1480,12 @@ int gol_plan_units(int64_t rows, int64_t words, int k, int tile_rows, int32_t *o
         for (int j = 0; j < kMaxNeighbours; ++j) o[8 + j] = j < u.nnb ? u.nb[j] : -1;
         o[8 + kMaxNeighbours] = u.cost;
     }
+    return GOL_OK;
+}
+
+int gol_kernel_launches(uint64_t *out) {
+    if (!out) return fail(GOL_EINVAL, "null output");
+    *out = launches_so_far();
     return GOL_OK;
 }
 

@@ -168,6 +168,14 @@ cudaError_t launch_persistent(const PersistArgs &a, bool torus, int variant, int
 template <int K>
 cudaError_t persistent_occupancy(bool torus, int variant, int *blocks_per_sm);
 
+// Kernel launch count of the process (kernels_util.cu): every launcher adds
+// the kernels it launches; launches recorded into a CUDA graph while the
+// library captures one are not counted (set_capturing), each replay of such
+// a graph adds the graph's kernel count instead.
+void count_launches(int n);
+void set_capturing(bool on);
+uint64_t launches_so_far();
+
 // Utility kernels (kernels_util.cu).
 cudaError_t launch_sched_init(const PersistArgs &a, int nboards, cudaStream_t s);
 cudaError_t launch_byte_step(const uint8_t *in, uint8_t *out, int64_t R, int64_t C, int torus,

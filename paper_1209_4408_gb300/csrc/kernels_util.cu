@@ -1,5 +1,6 @@
 // Byte-per-cell step, layout conversion, population count, scheduler
 // initialisation and the integer-throughput probe.
+#include <atomic>
 #include <cooperative_groups.h>
 
 #include "gol_internal.h"
@@ -523,50 +524,67 @@ __global__ void int_probe_kernel(unsigned *sink, int iters) {
     if (acc == 0x12345678u) sink[blockIdx.x] = acc;   // keeps the chains live
 }
 
+std::atomic<uint64_t> g_launch_count{0};
+thread_local bool t_capturing = false;
+
 }  // namespace
+
+void count_launches(int n) {
+    if (!t_capturing) g_launch_count.fetch_add((uint64_t)n, std::memory_order_relaxed);
+}
+void set_capturing(bool on) { t_capturing = on; }
+uint64_t launches_so_far() { return g_launch_count.load(std::memory_order_relaxed); }
 
 cudaError_t launch_sched_init(const PersistArgs &a, int nboards, cudaStream_t s) {
     const int64_t n = max(max((int64_t)a.nunits, (int64_t)a.total_tasks), (int64_t)max(nboards, 32));
     sched_init_kernel<<<grid_for(n, kBlock, 4096), kBlock, 0, s>>>(a, nboards);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_byte_step(const uint8_t *in, uint8_t *out, int64_t R, int64_t C, int torus,
                              cudaStream_t s) {
     byte_step_kernel<<<grid_for(R * C), kBlock, 0, s>>>(in, out, R, C, torus);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const uint8_t *cells, uint64_t *words, int64_t R, int64_t W, int32_t *bad,
                         cudaStream_t s) {
     pack_kernel<<<grid_for(R * W), kBlock, 0, s>>>(cells, words, R * W, bad);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_check_bytes(const uint8_t *cells, int64_t n, int32_t *bad, cudaStream_t s) {
     check_bytes_kernel<<<grid_for(n), kBlock, 0, s>>>(cells, n, bad);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(const uint64_t *words, uint8_t *cells, int64_t R, int64_t W, cudaStream_t s) {
     unpack_kernel<<<grid_for(R * W), kBlock, 0, s>>>(words, cells, R * W);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_region_packed(const uint64_t *words, int64_t R, int64_t C, int64_t r0, int64_t c0,
                                  int64_t nr, int64_t nc, uint8_t *out, bool transposed, cudaStream_t s) {
     region_packed_kernel<<<grid_for(nr * nc), kBlock, 0, s>>>(words, R, C, r0, c0, nr, nc, out, transposed);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack_transposed(const uint8_t *cells, int64_t R, int64_t C, uint64_t *store, int32_t *bad,
                                    cudaStream_t s) {
     if (R * C > 0) pack_transposed_kernel<<<grid_for((R / 64) * C), kBlock, 0, s>>>(cells, R, C, store, bad);
+    if (R * C > 0) count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpack_transposed(const uint64_t *store, int64_t R, int64_t C, uint8_t *cells, cudaStream_t s) {
     if (R * C > 0) unpack_transposed_kernel<<<grid_for((R / 64) * C), kBlock, 0, s>>>(store, R, C, cells);
+    if (R * C > 0) count_launches(1);
     return cudaGetLastError();
 }
 
@@ -576,8 +594,10 @@ cudaError_t launch_orient(const uint64_t *src, uint64_t *dst, int64_t R, int64_t
     if (transposed) {
         const int64_t nsuper = ((R / 64 + kSuper - 1) / kSuper) * ((W + kSuper - 1) / kSuper);
         orient_super_kernel<<<(unsigned)nsuper, kBlock, 0, s>>>(src, dst, R, W, to_res);
+        count_launches(1);
     } else {
         orient_kernel<<<grid_for(R * W, kBlock, 1 << 16), kBlock, 0, s>>>(src, dst, R, W, to_res);
+        count_launches(1);
     }
     return cudaGetLastError();
 }
@@ -585,35 +605,41 @@ cudaError_t launch_orient(const uint64_t *src, uint64_t *dst, int64_t R, int64_t
 cudaError_t launch_region_bytes(const uint8_t *cells, int64_t R, int64_t C, int64_t r0, int64_t c0,
                                 int64_t nr, int64_t nc, uint8_t *out, cudaStream_t s) {
     region_bytes_kernel<<<grid_for(nr * nc), kBlock, 0, s>>>(cells, R, C, r0, c0, nr, nc, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_popcount_packed(const uint64_t *words, int64_t n, unsigned long long *out,
                                    cudaStream_t s) {
     popcount_kernel<uint64_t><<<grid_for(n, kBlock, 8192), kBlock, 0, s>>>(words, n, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_popcount_bytes(const uint8_t *cells, int64_t n, unsigned long long *out,
                                   cudaStream_t s) {
     popcount_kernel<uint8_t><<<grid_for(n, kBlock, 8192), kBlock, 0, s>>>(cells, n, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_convert(const uint64_t *src, uint64_t *dst, int64_t n, bool to_res, cudaStream_t s) {
     if (n > 0) convert_kernel<<<grid_for(n, kBlock, 1 << 16), kBlock, 0, s>>>(src, dst, n, to_res);
+    if (n > 0) count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter_boards(const CopyDesc *d, const int32_t *block_board, int64_t blocks, const uint64_t *staging,
                                   cudaStream_t s) {
     if (blocks > 0) scatter_boards_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(d, block_board, staging);
+    if (blocks > 0) count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_boards(const CopyDesc *d, const int32_t *block_board, int64_t blocks, uint64_t *staging,
                                  cudaStream_t s) {
     if (blocks > 0) gather_boards_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(d, block_board, staging);
+    if (blocks > 0) count_launches(1);
     return cudaGetLastError();
 }
 
@@ -656,6 +682,7 @@ cudaError_t launch_byte_cluster(const uint8_t *in, uint8_t *out, int64_t R, int6
                                              (int)smem);
         if (e != cudaSuccess) return e;
         byte_resident_kernel<false><<<1, threads, smem, s>>>(in, out, (int)R, (int)C, torus, G);
+        count_launches(1);
         return cudaGetLastError();
     }
     cudaError_t e = cudaFuncSetAttribute(byte_resident_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -673,11 +700,14 @@ cudaError_t launch_byte_cluster(const uint8_t *in, uint8_t *out, int64_t R, int6
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, byte_resident_kernel<true>, in, out, (int)R, (int)C, torus, G);
+    e = cudaLaunchKernelEx(&cfg, byte_resident_kernel<true>, in, out, (int)R, (int)C, torus, G);
+    if (e == cudaSuccess) count_launches(1);
+    return e;
 }
 
 cudaError_t launch_int_probe(unsigned *sink, int iters, int grid, int block, cudaStream_t s) {
     int_probe_kernel<<<grid, block, 0, s>>>(sink, iters);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -944,6 +944,7 @@ cudaError_t launch_persistent_impl(const PersistArgs &a, bool torus, int variant
         else
             persistent_step_kernel<K, false, 2><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
     }
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -53,7 +53,7 @@ EXPORTED = (
     "gol_sync",
     "gol_set_stream", "gol_set_allocator", "gol_last_error", "gol_set_option", "gol_get_option",
     "gol_tune_set", "gol_tune_get", "gol_tune_reset", "gol_device_info", "gol_probe_int_throughput",
-    "gol_debug_unfilled_wait", "gol_step_packed_noalloc", "gol_plan_units",
+    "gol_debug_unfilled_wait", "gol_step_packed_noalloc", "gol_plan_units", "gol_kernel_launches",
 )
 
 
@@ -112,6 +112,7 @@ def load() -> ctypes.CDLL:
         "gol_debug_unfilled_wait": [i64],
         "gol_step_packed_noalloc": [vp, vp, i64, i64, i32, i64, vp],
         "gol_plan_units": [i64, i64, i32, i32, P(i32), ctypes.c_size_t, P(ctypes.c_size_t)],
+        "gol_kernel_launches": [P(ctypes.c_uint64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -379,6 +380,13 @@ def gol_probe_int_throughput():
     ops, sec = ctypes.c_double(), ctypes.c_double()
     _check(load().gol_probe_int_throughput(ctypes.byref(ops), ctypes.byref(sec)))
     return ops.value, sec.value
+
+
+def gol_kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    v = ctypes.c_uint64()
+    _check(load().gol_kernel_launches(ctypes.byref(v)))
+    return v.value
 
 
 def gol_debug_unfilled_wait(timeout_ms: int) -> int:

@@ -3,20 +3,32 @@
 Requests (a board, its initial cells, a generation count) arrive over time.
 The server keeps every admitted board resident on the device, admits waiting
 requests in arrival order while their two device buffers fit the memory
-budget, and advances all admitted boards together, one
-``gol_step_batch`` launch per tick.  Each tick gives every active board a
-quantum of generations (at most what it still needs); the quantum adapts so
-that a tick lasts about ``tick_target_s``.  Requests that arrive while a tick
-runs are admitted (created and uploaded) before the next tick; boards that
-reach their generation count are read back and freed at the end of the tick
-that finished them.  The stepping itself is the library's persistent launch,
-so the result of every request is bit-identical to stepping it alone.
+budget, and advances all admitted boards together, one ``gol_step_batch``
+launch per tick.  Each tick gives every active board a quantum of
+generations (at most what it still needs); the quantum adapts so that a tick
+lasts about ``tick_target_s`` of device time.  The stepping itself is the
+library's persistent launch, so the result of every request is
+bit-identical to stepping it alone.
+
+The loop never waits for the device while there is something to queue:
+ticks are launched ahead (up to ``depth`` in flight on the library's
+stream).  The host knows which boards a tick finishes when it launches it
+(each board's remaining generations are host state), so a finished board's
+result copy is queued right behind that tick and the next tick, without
+those boards, is queued right after.  An event recorded behind each tick
+tells the host when the tick, and the copies of the boards it finished, are
+done; only then are those requests answered, their boards destroyed and
+their memory returned to the budget.  Arrivals are admitted (created, and
+their cells uploaded from page-locked memory) between launches, so their
+uploads queue behind the ticks already in flight and they join the next
+tick launched.
 
 ``serve_fcfs`` is the baseline that serves the same trace one request at a
 time with ``gol_step``.
 """
 from __future__ import annotations
 
+import collections
 import time
 from dataclasses import dataclass, field
 from typing import Callable, Sequence
@@ -34,11 +46,13 @@ class Job:
     cols: int
     gens: int
     words: np.ndarray                 # initial packed cells (host)
-    remaining: int = 0
+    remaining: int = 0                # generations not yet queued on the device
     handle: int | None = None
     admitted_s: float | None = None
     done_s: float | None = None
     result: np.ndarray | None = None
+    staged: object = None             # host memory the upload reads from (kept until retired)
+    pending: object = None            # the queued result copy
 
     @property
     def bytes_on_device(self) -> int:
@@ -58,6 +72,7 @@ class ServeStats:
     max_active: int = 0
     max_waiting: int = 0
     peak_bytes: int = 0
+    device_s: float = 0.0             # device time of the ticks (0 when the backend cannot tell)
 
     def summary(self) -> dict:
         lat = np.array(self.latencies_s) if self.latencies_s else np.zeros(1)
@@ -72,47 +87,133 @@ class ServeStats:
             "max_active": self.max_active,
             "max_waiting": self.max_waiting,
             "peak_device_bytes": self.peak_bytes,
+            "device_busy": self.device_s / max(self.makespan_s, 1e-9),
         }
+
+
+class GpuBackend:
+    """The library on the GPU plus the stream plumbing the loop needs:
+    events and copies on the library's stream (PyTorch's current stream,
+    which ``gol.use_torch_allocator`` makes the library's), page-locked
+    staging of uploads and asynchronous result copies."""
+
+    def __init__(self):
+        import torch
+
+        self.torch = torch
+        self.stream = torch.cuda.current_stream()
+        gol.gol_set_stream(self.stream)     # library work, events and copies on one stream
+
+    def gol_create_ex(self, rows, cols, torus, layout):
+        return gol.gol_create_ex(rows, cols, torus, layout)
+
+    def stage(self, words: np.ndarray):
+        """Page-locked copy of a request's cells (the upload then runs
+        asynchronously on the stream)."""
+        t = self.torch.empty(words.size, dtype=self.torch.int64, pin_memory=True)
+        v = t.numpy().view(np.uint64)
+        v[:] = words.reshape(-1)
+        return t, v.reshape(words.shape)
+
+    def gol_set_packed(self, h, words):
+        gol.gol_set_packed(h, words)
+
+    def gol_step_batch(self, hs, gens):
+        gol.gol_step_batch(hs, gens)
+
+    def gol_destroy(self, h):
+        gol.gol_destroy(h)
+
+    def download(self, h, rows, cols):
+        """Queues the copy of board h's current state to page-locked host
+        memory; the returned object's ``result()`` is valid once an event
+        recorded afterwards has completed."""
+        torch = self.torch
+        n = rows * (cols // 64)
+        dev = torch.empty(n, dtype=torch.int64, device="cuda")
+        gol.gol_get_packed_device(h, dev.data_ptr(), n)
+        host = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        host.copy_(dev, non_blocking=True)
+        return _Pending(host, rows, cols // 64)
+
+    def record(self):
+        ev = self.torch.cuda.Event(enable_timing=True)
+        ev.record(self.stream)
+        return ev
+
+    def done(self, ev) -> bool:
+        return ev.query()
+
+    def wait(self, ev):
+        ev.synchronize()
+
+    def elapsed_s(self, a, b) -> float:
+        return a.elapsed_time(b) * 1e-3
+
+
+class _Pending:
+    def __init__(self, host, rows, words):
+        self.host, self.shape = host, (rows, words)
+
+    def result(self) -> np.ndarray:
+        return self.host.numpy().view(np.uint64).reshape(self.shape).copy()
+
+
+@dataclass
+class _Tick:
+    start: object
+    end: object
+    finishing: list
+    cells_gens: int
 
 
 class Server:
     def __init__(self, budget_bytes: int = 120 << 30, tick_target_s: float = 0.02,
                  quantum_min: int = 8, quantum_max: int = 1 << 16, keep_results: bool = False,
-                 clock: Callable[[], float] = time.perf_counter, backend=None):
-        self.g = backend if backend is not None else gol
+                 clock: Callable[[], float] = time.perf_counter, backend=None, depth: int = 2,
+                 sleep: Callable[[float], None] = time.sleep, poll_s: float = 2e-4):
+        self.g = backend if backend is not None else GpuBackend()
         self.budget = budget_bytes
         self.tick_target = tick_target_s
         self.qmin, self.qmax = quantum_min, quantum_max
         self.keep = keep_results
         self.clock = clock
+        self.depth = max(1, depth)
+        self.sleep = sleep
+        self.poll = poll_s
         self.quantum = quantum_min
-        self.rate_cups = None             # measured cell updates per second
+        self.rate_cups = None             # measured cell updates per second of device time
+        self._per_gen = 0                 # cells of the boards in the last tick
 
     def _admit(self, job: Job, now: float):
         job.handle = self.g.gol_create_ex(job.rows, job.cols, True, gol.GOL_LAYOUT_PACKED)
-        self.g.gol_set_packed(job.handle, job.words)
+        words = job.words
+        if hasattr(self.g, "stage"):
+            job.staged, words = self.g.stage(job.words)
+        self.g.gol_set_packed(job.handle, words)
         job.remaining = job.gens
         job.admitted_s = now
 
     def _retire(self, job: Job, now: float, stats: ServeStats):
-        if self.keep:
-            job.result = self.g.gol_get_packed(job.handle)
-        else:
-            self.g.gol_sync(job.handle)
+        if job.pending is not None:
+            r = job.pending.result()
+            job.result = r if self.keep else None
+            job.pending = None
         self.g.gol_destroy(job.handle)
         job.handle = None
+        job.staged = None
         job.done_s = now
         stats.latencies_s.append(now - job.arrival_s)
 
     def run(self, jobs: Sequence[Job]) -> ServeStats:
-        """Serves ``jobs`` (sorted by arrival) against the wall clock.  If a
-        library call fails, the boards of the admitted requests are freed
-        before the error propagates."""
-        active: list[Job] = []
+        """Serves ``jobs`` against the clock.  If a library call fails, the
+        boards of the admitted requests are released before the error
+        propagates."""
+        live: list[Job] = []
         try:
-            return self._run(jobs, active)
+            return self._run(jobs, live)
         except BaseException:
-            for j in active:
+            for j in live:
                 if j.handle is not None:
                     try:
                         self.g.gol_destroy(j.handle)
@@ -121,69 +222,87 @@ class Server:
                     j.handle = None
             raise
 
-    def _run(self, jobs: Sequence[Job], active: list) -> ServeStats:
+    def _run(self, jobs: Sequence[Job], live: list) -> ServeStats:
         jobs = sorted(jobs, key=lambda j: j.arrival_s)
         stats = ServeStats()
-        waiting: list[Job] = []
+        waiting: collections.deque = collections.deque()
+        inflight: collections.deque = collections.deque()
+        active: list[Job] = []            # admitted, generations left to queue
         used = 0
         nxt = 0
         t0 = self.clock()
-        while nxt < len(jobs) or waiting or active:
+        while nxt < len(jobs) or waiting or active or inflight:
+            # ticks that completed, oldest first: answer the requests they finished
+            while inflight and self.g.done(inflight[0].end):
+                tk = inflight.popleft()
+                now = self.clock() - t0
+                for j in tk.finishing:
+                    self._retire(j, now, stats)
+                    used -= j.bytes_on_device
+                    live.remove(j)
+                self._observe(tk, stats)
             now = self.clock() - t0
             while nxt < len(jobs) and jobs[nxt].arrival_s <= now:
                 waiting.append(jobs[nxt])
                 nxt += 1
             while waiting and used + waiting[0].bytes_on_device <= self.budget:
-                j = waiting.pop(0)
-                active.append(j)
+                j = waiting.popleft()
+                live.append(j)
                 self._admit(j, now)
+                active.append(j)
                 used += j.bytes_on_device
-            if waiting and not active:
+            if waiting and not live:
                 raise RuntimeError("request %d needs %d bytes, more than the budget" %
                                    (waiting[0].rid, waiting[0].bytes_on_device))
             stats.max_waiting = max(stats.max_waiting, len(waiting))
             stats.max_active = max(stats.max_active, len(active))
             stats.peak_bytes = max(stats.peak_bytes, used)
-            if not active:
-                if nxt < len(jobs):                       # idle until the next arrival
-                    time.sleep(max(0.0, min(jobs[nxt].arrival_s - (self.clock() - t0), 0.01)))
+            if active and len(inflight) < self.depth:
+                self._launch(active, inflight, stats)
                 continue
-            # one tick: every active board advances by min(remaining, quantum)
-            q = [min(j.remaining, self.quantum) for j in active]
-            cells_gens = sum(j.rows * j.cols * g for j, g in zip(active, q))
-            t_tick = self.clock()
-            self.g.gol_step_batch([j.handle for j in active], q)
-            # admit arrivals while the tick runs (uploads queue behind it)
-            now = self.clock() - t0
-            while nxt < len(jobs) and jobs[nxt].arrival_s <= now:
-                waiting.append(jobs[nxt])
-                nxt += 1
-            self.g.gol_sync(active[0].handle)
-            dt = self.clock() - t_tick
-            stats.ticks += 1
-            stats.cell_updates += cells_gens
-            now = self.clock() - t0
-            still = []
-            for j, g in zip(active, q):
-                j.remaining -= g
-                if j.remaining == 0:
-                    self._retire(j, now, stats)
-                    used -= j.bytes_on_device
-                else:
-                    still.append(j)
-            active[:] = still
-            self._adapt(cells_gens, dt, active)
+            if not inflight and not active and nxt < len(jobs):
+                # idle until the next arrival
+                self.sleep(max(0.0, min(jobs[nxt].arrival_s - (self.clock() - t0), 0.01)))
+            elif inflight:
+                self.sleep(self.poll)
         stats.makespan_s = self.clock() - t0
         return stats
 
-    def _adapt(self, cells_gens: int, dt: float, active: Sequence[Job]):
-        if dt > 0 and cells_gens > 0:
-            r = cells_gens / dt
+    def _launch(self, active: list, inflight: collections.deque, stats: ServeStats):
+        """One tick: every active board advances by min(remaining, quantum);
+        boards that reach their count have their result copy queued behind it."""
+        q = [min(j.remaining, self.quantum) for j in active]
+        cells_gens = sum(j.rows * j.cols * g for j, g in zip(active, q))
+        self._per_gen = sum(j.rows * j.cols for j in active)
+        start = self.g.record()
+        self.g.gol_step_batch([j.handle for j in active], q)
+        finishing, still = [], []
+        for j, g in zip(active, q):
+            j.remaining -= g
+            if j.remaining == 0:
+                j.pending = self.g.download(j.handle, j.rows, j.cols)
+                finishing.append(j)
+            else:
+                still.append(j)
+        active[:] = still
+        inflight.append(_Tick(start, self.g.record(), finishing, cells_gens))
+        stats.ticks += 1
+        stats.cell_updates += cells_gens
+
+    def _observe(self, tk: _Tick, stats: ServeStats):
+        """Device time of a completed tick; adapts the quantum so that a tick
+        lasts about tick_target_s."""
+        dt = self.g.elapsed_s(tk.start, tk.end)
+        stats.device_s += dt
+        if dt > 0 and tk.cells_gens > 0:
+            r = tk.cells_gens / dt
             self.rate_cups = r if self.rate_cups is None else 0.7 * self.rate_cups + 0.3 * r
-        if not active or not self.rate_cups:
+        self._adapt()
+
+    def _adapt(self):
+        if not self.rate_cups or not self._per_gen:
             return
-        per_gen = sum(j.rows * j.cols for j in active)
-        q = int(self.tick_target * self.rate_cups / max(per_gen, 1))
+        q = int(self.tick_target * self.rate_cups / max(self._per_gen, 1))
         q = max(self.qmin, min(self.qmax, q))
         self.quantum = max(self.qmin, (q // 8) * 8)
 

@@ -56,6 +56,20 @@ class FakeBackend:
         b = self.boards.pop(h)
         self.live_bytes -= 2 * b["rows"] * b["cols"] // 8
 
+    # stream plumbing of the event-driven loop: work completes at once
+    def download(self, h, rows, cols):
+        gen = self.boards[h]["gen"]
+        return type("Pending", (), {"result": lambda self_: gen})()
+
+    def record(self):
+        return None
+
+    def done(self, ev):
+        return True
+
+    def elapsed_s(self, a, b):
+        return 0.0
+
 
 def make_jobs(serve, n, rate, seed=3, side_hi=512, gen_hi=300):
     reqs = synth.request_stream(n, rate, seed=seed, side_hi=side_hi, gen_lo=5, gen_hi=gen_hi)
@@ -111,8 +125,8 @@ def test_host_logic_frees_boards_when_a_step_fails(serve_mod, fail_at):
 
 
 class TickClock:
-    """Deterministic clock: each reading advances by `dt`; a batch step
-    advances it by `tick` (the device time of the step)."""
+    """Deterministic clock: each reading advances by `dt`, a sleep by its
+    length; a batch step occupies the modelled device for `tick` seconds."""
 
     def __init__(self, dt=1e-5, tick=5e-3):
         self.t, self.dt, self.tick = 0.0, dt, tick
@@ -124,9 +138,15 @@ class TickClock:
             self.first = self.t
         return self.t
 
+    def sleep(self, s):
+        self.t += s
+
 
 class ClockedBackend(FakeBackend):
-    """Records, per batch step, its start time and the requests in it."""
+    """A modelled device stream: a batch step starts when the work queued
+    before it has finished and lasts one tick; an event completes when the
+    clock passes the point of the stream where it was recorded.  Records,
+    per batch step, its start time and the requests in it."""
 
     def __init__(self, clock, jobs):
         super().__init__()
@@ -134,37 +154,56 @@ class ClockedBackend(FakeBackend):
         self.rid_of_words = {id(j.words): j.rid for j in jobs}
         self.rid_of = {}
         self.ticks = []
+        self.free_at = 0.0              # the modelled stream is idle from then on
 
     def gol_set_packed(self, h, words):
         super().gol_set_packed(h, words)
         self.rid_of[h] = self.rid_of_words[id(words)]
 
     def gol_step_batch(self, hs, gens):
-        self.ticks.append((self.clock.t - self.clock.first, {self.rid_of[h] for h in hs}))
+        start = max(self.clock.t, self.free_at)
+        self.ticks.append((start - self.clock.first, {self.rid_of[h] for h in hs}))
         super().gol_step_batch(hs, gens)
-        self.clock.t += self.clock.tick
+        self.free_at = start + self.clock.tick
+
+    def record(self):
+        return max(self.clock.t, self.free_at)
+
+    def done(self, ev):
+        return self.clock.t >= ev
+
+    def elapsed_s(self, a, b):
+        return b - a
 
 
 def test_host_logic_admits_arrivals_at_the_next_tick(serve_mod):
-    """Continuous batching on a deterministic clock: a request that arrives
-    while boards are stepping joins the next tick (memory permitting), so it
-    waits at most one tick plus host time; every request gets exactly its
-    generations; ticks hold several requests at once."""
+    """Continuous batching on a deterministic clock: ticks are queued ahead
+    (two in flight), so a request that arrives while boards are stepping
+    joins the next tick launched (memory permitting) and waits at most two
+    ticks plus host time; the modelled device never idles while requests
+    remain; every request gets exactly its generations; ticks hold several
+    requests at once."""
     clock = TickClock()
     jobs = make_jobs(serve_mod, 30, rate=400.0, gen_hi=400)       # arrivals over ~75 ms; 5 ms ticks
     fake = ClockedBackend(clock, jobs)
     srv = serve_mod.Server(budget_bytes=1 << 40, tick_target_s=5e-3, quantum_min=8, keep_results=True,
-                           clock=clock, backend=fake)
+                           clock=clock, backend=fake, sleep=clock.sleep)
     st = srv.run(jobs)
     assert st.summary()["requests"] == len(jobs)
     assert all(j.result == j.gens for j in jobs) and not fake.boards
-    host = 200 * clock.dt                                           # generous bound on host readings per tick
+    host = 200 * clock.dt + srv.poll                                # host readings and one poll per tick
     for j in jobs:
         first = next(t for t, rids in fake.ticks if j.rid in rids)
         assert j.arrival_s <= first + 1e-12
-        assert first - j.arrival_s <= clock.tick + host, (j.rid, j.arrival_s, first)
-        assert j.arrival_s <= j.admitted_s <= first + 1e-12 and j.done_s >= first
+        assert first - j.arrival_s <= 2 * clock.tick + host, (j.rid, j.arrival_s, first)
+        assert j.arrival_s <= j.admitted_s <= first + 1e-12 and j.done_s >= first + clock.tick - 1e-12
     assert max(len(rids) for _, rids in fake.ticks) > 1 and st.ticks >= 10
+    # back to back: once the first request is in, a tick starts as soon as the
+    # previous one ends (until the stream runs dry between arrivals)
+    starts = [t for t, _ in fake.ticks]
+    gaps = [b - (a + clock.tick) for a, b in zip(starts, starts[1:])]
+    assert min(gaps) >= -1e-12
+    assert sum(g < 1e-9 for g in gaps) >= len(gaps) // 2
 
 
 @pytest.mark.gpu
