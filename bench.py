@@ -52,15 +52,17 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-probe", action="store_true", help="skip the integer-throughput probe")
-    ap.add_argument("--serve-requests", type=int, default=600,
-                    help="requests of the served run added to the batch line (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the served runs added to the batch line (0 = skip)")
     ap.add_argument("--serve-load", type=float, default=0.7,
                     help="offered load of the served run as a fraction of the measured batched GCUPS")
     ap.add_argument("--serve-sweep", action="store_true",
-                    help="also serve the stream at offered loads 0.3 / 0.7 / 1.0 and at 0.7 under a 32 MiB "
-                         "budget (about half the boards the unconstrained run holds at its peak)")
-    ap.add_argument("--fcfs-requests", type=int, default=24,
-                    help="requests of the same trace served one at a time (baseline)")
+                    help="also serve the stream at offered loads 0.3 and 0.5")
+    ap.add_argument("--no-fcfs", dest="fcfs", action="store_false",
+                    help="skip serving the same trace one request at a time (baseline)")
+    ap.add_argument("--no-sub", action="store_true", help="skip the single-board sub-lines (16384^2, 131072^2)")
+    ap.add_argument("--no-cpu-configs", action="store_true",
+                    help="skip the per-configuration serial / OpenMP oracle baselines")
     return ap.parse_args()
 
 
@@ -185,9 +187,9 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU baseline: the oracle on a bounded sample
+# CPU baselines: the oracle (serial, and its OpenMP row decomposition)
 # ---------------------------------------------------------------------------
-CPU_SAMPLE_SIDE = 2048   # larger boards are timed on a crop of this side
+CPU_SAMPLE_SIDE = 2048   # larger boards are timed on a crop of this side (serial oracle)
 CROP_NOTE = "; boards above %d^2 cells timed on their top-left %d x %d corner as a torus" % (
     CPU_SAMPLE_SIDE, CPU_SAMPLE_SIDE, CPU_SAMPLE_SIDE)
 
@@ -201,6 +203,20 @@ def oracle_sample_cells(s):
         nr, nc = min(s.rows, CPU_SAMPLE_SIDE), min(s.cols, CPU_SAMPLE_SIDE)
         return synth.bernoulli_region(s.rows, s.cols, s.density, s.seed, 0, 0, nr, nc), True
     return synth.bernoulli_board(s.rows, s.cols, s.density, s.seed), False
+
+
+def spec_cells(s):
+    """The full initial cells of board spec ``s`` (uint8)."""
+    if s.density == 0.5 and s.cols % 64 == 0:
+        import oracle
+
+        out = np.empty((s.rows, s.cols), dtype=np.uint8)
+        step = max(1, (1 << 22) // s.cols)
+        for r0 in range(0, s.rows, step):
+            r1 = min(s.rows, r0 + step)
+            out[r0:r1] = oracle.unpack_words(synth.random_words(r1 - r0, s.cols // 64, s.seed, row0=r0))
+        return out
+    return synth.bernoulli_board(s.rows, s.cols, s.density, s.seed)
 
 
 def cpu_oracle_sample(specs, seconds: float, threads: int = 1):
@@ -236,37 +252,237 @@ def cpu_oracle_sample(specs, seconds: float, threads: int = 1):
     return done_cells / used / 1e9, threads, desc
 
 
+def host_facts():
+    """Host cores and CPU model, for the CPU baselines."""
+    import platform
+
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count() or 1, "cpu_model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
+def cpu_baselines(cfg_seconds: float = 120.0):
+    """The oracle on the host cores, on the seeded inputs of the GPU
+    workloads: the serial program (one core) and its OpenMP row
+    decomposition (Section 2.1) on every core.  256^2 byte board: all 1000
+    generations.  16384^2 board: OpenMP 100 generations of the whole board
+    (in chunks of 10, stopping early after ``cfg_seconds``), serial on its
+    top-left 2048^2 corner for 10 generations.  4096-board batch: 256 boards
+    (every 16th), min(gens, 8) generations each (OpenMP) and min(gens, 2)
+    (serial).  Returns {config: {"serial": ..., "openmp_rows": ...}}."""
+    import oracle
+
+    oracle.build()
+    nproc = os.cpu_count() or 1
+    out = {}
+
+    def timed(fn):
+        t = time.perf_counter()
+        fn()
+        return time.perf_counter() - t
+
+    # 256 x 256 byte board, Bernoulli(0.3), all 1000 generations
+    s = workload_specs("bytes", 1)[0][0]
+    c = synth.bernoulli_board(s.rows, s.cols, s.density, s.seed)
+    n = c.size * s.gens
+    out["bytes_256"] = {
+        "serial": {"value": round(n / timed(lambda: oracle.run(c, s.gens)) / 1e9, 5), "cores": 1,
+                   "sample": "the whole board, all %d generations" % s.gens},
+        "openmp_rows": {"value": round(n / timed(lambda: oracle.run_rows_omp(c, s.gens, nproc)) / 1e9, 5),
+                        "cores": nproc, "sample": "the whole board, all %d generations" % s.gens}}
+    # 16384^2 board
+    s = workload_specs("single", 1)[0][0]
+    c = spec_cells(s)
+    done, t_omp = 0, 0.0
+    x = c
+    while done < 100 and t_omp < cfg_seconds:
+        t = time.perf_counter()
+        x = oracle.run_rows_omp(x, 10, nproc)
+        t_omp += time.perf_counter() - t
+        done += 10
+    crop = np.ascontiguousarray(c[:CPU_SAMPLE_SIDE, :CPU_SAMPLE_SIDE])
+    t_ser = timed(lambda: oracle.run(crop, 10))
+    out["single_16384"] = {
+        "serial": {"value": round(crop.size * 10 / t_ser / 1e9, 5), "cores": 1,
+                   "sample": "top-left %d^2 corner as a torus, 10 generations" % CPU_SAMPLE_SIDE},
+        "openmp_rows": {"value": round(c.size * done / t_omp / 1e9, 5), "cores": nproc,
+                        "sample": "the whole board, %d generations" % done}}
+    del c, x, crop
+    # 256 boards of the 4096-board batch
+    specs = workload_specs("batch", 4096)[0][::16]
+    boards = [synth.bernoulli_board(s.rows, s.cols, s.density, s.seed) for s in specs]
+    n8 = sum(b.size * min(s.gens, 8) for b, s in zip(boards, specs))
+    n2 = sum(b.size * min(s.gens, 2) for b, s in zip(boards, specs))
+    t8 = timed(lambda: [oracle.run_rows_omp(b, min(s.gens, 8), nproc) for b, s in zip(boards, specs)])
+    t2 = timed(lambda: [oracle.run(b, min(s.gens, 2)) for b, s in zip(boards, specs)])
+    out["batch_4096"] = {
+        "serial": {"value": round(n2 / t2 / 1e9, 5), "cores": 1,
+                   "sample": "256 boards (every 16th), min(gens, 2) generations each"},
+        "openmp_rows": {"value": round(n8 / t8 / 1e9, 5), "cores": nproc,
+                        "sample": "256 boards (every 16th), min(gens, 8) generations each"}}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # served request stream (continuous batching)
 # ---------------------------------------------------------------------------
-def served_run(gol, n_req, load, capacity_gcups, budget_bytes, fcfs_n, seed=synth.SEED_SERVE):
+SERVE_WORKLOAD = ("Poisson arrivals; sides log-uniform [32, 8192] rounded to x64; density U(0.1,0.6); "
+                  "gens log-uniform [10, 1e5]; the first %d requests of the seeded stream")
+
+
+def request_words(reqs):
+    """Initial cells of every request (generated on all host cores)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+        return list(ex.map(lambda r: synth.bernoulli_words(r.rows, r.cols, r.density, r.seed), reqs))
+
+
+def stream_jobs(n_req, rate, words, seed=synth.SEED_SERVE):
+    """The first n_req requests of the seeded stream at `rate` per second
+    (sizes, densities and generation counts do not depend on the rate)."""
+    from paper_1209_4408_gb300 import serve
+
+    reqs = synth.request_stream(n_req, rate, seed=seed)
+    return [serve.Job(r.index, r.arrival_s, r.rows, r.cols, r.gens, w) for r, w in zip(reqs, words)]
+
+
+def served_run(n_req, load, capacity_gcups, budget_bytes, words, fcfs=False, seed=synth.SEED_SERVE):
     """Poisson request stream at `load` x the measured batched capacity,
-    served by the continuous-batching loop; then a prefix of the same trace
-    served one request at a time."""
+    served by the continuous-batching loop (and, if `fcfs`, the same trace
+    served one request at a time)."""
     from paper_1209_4408_gb300 import serve
 
     probe = synth.request_stream(n_req, 1.0, seed=seed)
     mean_work = sum(r.work for r in probe) / max(1, len(probe))
     rate = load * capacity_gcups * 1e9 / mean_work
-    reqs = synth.request_stream(n_req, rate, seed=seed)
-    jobs = [serve.Job(r.index, r.arrival_s, r.rows, r.cols, r.gens,
-                      synth.bernoulli_words(r.rows, r.cols, r.density, r.seed)) for r in reqs]
+    jobs = stream_jobs(n_req, rate, words, seed)
     st = serve.Server(budget_bytes=budget_bytes).run(jobs)
     out = st.summary()
     out.update({"rate_per_s": round(rate, 3), "offered_load": load, "budget_bytes": budget_bytes,
-                "workload": "Poisson arrivals; sides log-uniform [32, 8192] rounded to x64; density U(0.1,0.6);"
-                            " gens log-uniform [10, 1e5]; first %d requests of the seeded stream" % n_req})
-    if fcfs_n > 0:
-        fj = [serve.Job(j.rid, j.arrival_s, j.rows, j.cols, j.gens, j.words) for j in jobs[:fcfs_n]]
+                "offered_gcups": round(load * capacity_gcups, 1), "workload": SERVE_WORKLOAD % n_req})
+    if fcfs:
+        fj = stream_jobs(n_req, rate, words, seed)
         fs = serve.serve_fcfs(fj).summary()
         out["fcfs"] = {k: fs[k] for k in ("requests", "p50_ms", "p99_ms", "mean_ms", "gcups", "makespan_s")}
-        out["fcfs"]["sample"] = "first %d requests of the same trace, one at a time with gol_step" % fcfs_n
+        out["fcfs"]["sample"] = "the same %d-request trace, one request at a time with gol_step" % n_req
     return out
 
 
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def device_bench(gol, specs, layout, steps, warmup, stream, local, barrier=None):
+    """Creates the boards of `specs`, times `steps` gol_step_batch calls of
+    all of them (after `warmup`), CUDA events on the library's stream, SM
+    clocks sampled meanwhile.  Returns (result dict, boards, pinned host
+    words or None)."""
+    import torch
+
+    pinned, boards = None, []
+    if layout == gol.GOL_LAYOUT_PACKED:
+        nwords = sum(s.rows * s.cols // 64 for s in specs)
+        pinned = torch.empty(nwords, dtype=torch.int64, pin_memory=True)
+        host = pinned.numpy().view(np.uint64)
+        views = []
+        off = 0
+        for s in specs:
+            n = s.rows * s.cols // 64
+            views.append((s, host[off:off + n].reshape(s.rows, s.cols // 64)))
+            off += n
+
+        def fill(item):
+            s, v = item
+            if s.seed == synth.SEED_HUGE_128K:
+                synth.glider_band_words(s.rows, s.cols // 64, s.seed, synth.GliderBand(), out=v)
+            elif s.density == 0.5:
+                synth.random_words(s.rows, s.cols // 64, s.seed, out=v)
+            else:
+                v[:] = synth.bernoulli_words(s.rows, s.cols, s.density, s.seed)
+
+        from concurrent.futures import ThreadPoolExecutor
+
+        with ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, views))
+        for s, v in views:
+            b = gol.Board(s.rows, s.cols, torus=True, layout=layout)
+            b.set_packed(v)
+            boards.append(b)
+    else:
+        for s in specs:
+            b = gol.Board(s.rows, s.cols, torus=True, layout=layout)
+            b.set(synth.bernoulli_board(s.rows, s.cols, s.density, s.seed))
+            boards.append(b)
+    handle_array = np.array([b.handle for b in boards], dtype=np.uint64)
+    gens_array = np.array([s.gens for s in specs], dtype=np.int64)
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        gol.gol_step_batch(handle_array, gens_array)
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with ClockSampler(local) as clk:
+        if barrier:
+            barrier()
+        torch.cuda.synchronize()
+        l0 = gol.gol_kernel_launches()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(steps):
+            ev[i][0].record(stream)
+            gol.gol_step_batch(handle_array, gens_array)
+            ev[i][1].record(stream)
+        t_end.record(stream)
+        launches = gol.gol_kernel_launches() - l0
+        if barrier:
+            barrier()
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    res = {"ms_total": t_start.elapsed_time(t_end), "step_ms": step_ms, "clocks": clk.summary(),
+           "launches": launches, "handles": handle_array, "gens": gens_array,
+           "cells_gens": sum(s.rows * s.cols * s.gens for s in specs),
+           "words_gens": sum(s.rows * (s.cols // 64) * s.gens for s in specs)}
+    return res, boards, pinned
+
+
+def roofline(gol, words_gens, mean_ms, peak_ops, workload):
+    """Integer-pipe roofline of the step kernel on the MEAN step time."""
+    achieved = words_gens * INT_OPS_PER_WORD_GEN / (mean_ms * 1e-3) / 1e12
+    peak = peak_ops / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
+            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(workload),
+            "peak_source": "integer-pipe probe (LOP3/funnel-shift mix) measured in this run",
+            "algorithmic_ops_per_launch": words_gens * INT_OPS_PER_WORD_GEN,
+            "time": "mean step (CUDA events on the launching stream)"}
+
+
+def sub_bench(gol, workload, steps, warmup, stream, local, peak_ops):
+    """One of the single-board workloads, timed on its own (a sub-object of
+    the batch line)."""
+    specs, desc = workload_specs(workload, 1)
+    res, boards, _ = device_bench(gol, specs, gol.GOL_LAYOUT_PACKED, steps, warmup, stream, local)
+    mean = sum(res["step_ms"]) / len(res["step_ms"])
+    k, rows = gol.gol_tune_get(specs[0].rows, specs[0].cols)
+    out = {"workload": desc, "value": round(res["cells_gens"] / (mean * 1e-3) / 1e9, 2), "unit": "GCUPS",
+           "steps": steps, "warmup": warmup, "ms_per_step": round(mean, 3),
+           "step_ms": [round(x, 3) for x in res["step_ms"]], "gens_per_pass": k, "tile_rows": rows,
+           "gpu_launches": res["launches"], "clocks": res["clocks"],
+           "roofline": roofline(gol, res["words_gens"], mean, peak_ops, workload)}
+    for b in boards:
+        b.close()
+    return out
+
+
 def run_gpu(args, rank, world, local):
     import torch
 
@@ -290,65 +506,17 @@ def run_gpu(args, rank, world, local):
 
     # ---- workload -----------------------------------------------------------
     specs, workload = workload_specs(args.workload, args.boards, rank)
-
-    total_cells_gens = sum(s.rows * s.cols * s.gens for s in specs)
-    total_words_gens = sum(s.rows * (s.cols // 64) * s.gens for s in specs)
     layout = gol.GOL_LAYOUT_BYTES if args.workload == "bytes" else gol.GOL_LAYOUT_PACKED
-    pinned, views, boards = None, [], []
-    if layout == gol.GOL_LAYOUT_PACKED:
-        nwords = sum(s.rows * s.cols // 64 for s in specs)
-        pinned = torch.empty(nwords, dtype=torch.int64, pin_memory=True)
-        host = pinned.numpy().view(np.uint64)
-        off = 0
-        for s in specs:
-            n = s.rows * s.cols // 64
-            v = host[off:off + n].reshape(s.rows, s.cols // 64)
-            if args.workload == "huge":
-                synth.glider_band_words(s.rows, s.cols // 64, s.seed, synth.GliderBand(), out=v)
-            elif s.density == 0.5:
-                synth.random_words(s.rows, s.cols // 64, s.seed, out=v)
-            else:
-                v[:] = synth.bernoulli_words(s.rows, s.cols, s.density, s.seed)
-            views.append(v)
-            off += n
-            b = gol.Board(s.rows, s.cols, torus=True, layout=layout)
-            b.set_packed(v)
-            boards.append(b)
-    else:
-        for s in specs:
-            b = gol.Board(s.rows, s.cols, torus=True, layout=layout)
-            b.set(synth.bernoulli_board(s.rows, s.cols, s.density, s.seed))
-            boards.append(b)
-    handles = [b.handle for b in boards]
-    handle_array = np.array(handles, dtype=np.uint64)   # built once, as a caller moving a batch every step would
-    gens = [s.gens for s in specs]
-    gens_array = np.array(gens, dtype=np.int64)
-    torch.cuda.synchronize()
+    res, boards, pinned = device_bench(gol, specs, layout, args.steps, args.warmup, stream, local, barrier)
+    handles, handle_array, gens_array = [b.handle for b in boards], res["handles"], res["gens"]
+    total_cells_gens, total_words_gens = res["cells_gens"], res["words_gens"]
+    step_ms = res["step_ms"]
+    ms = max_over_ranks(res["ms_total"] / args.steps, dist, "cuda")
+    mean_ms = sum(step_ms) / len(step_ms)
+    value = total_cells_gens * world / (ms * 1e-3) / 1e9
 
     def step():
         gol.gol_step_batch(handle_array, gens_array)
-
-    # ---- device-resident timing ------------------------------------------------
-    for _ in range(args.warmup):
-        step()
-    barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
-        barrier()
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
-        for i in range(args.steps):
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
-        t_end.record(stream)
-        barrier()
-    clocks = clk.summary()
-    ms_total = t_start.elapsed_time(t_end)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = max_over_ranks(ms_total / args.steps, dist, "cuda")
-    value = total_cells_gens * world / (ms * 1e-3) / 1e9
 
     # ---- plain loop: the same boards stepped one at a time -----------------------
     plain = None
@@ -374,6 +542,7 @@ def run_gpu(args, rank, world, local):
     if not args.no_e2e:
         e2e_steps = max(1, min(args.steps, 3))
         out_pinned = torch.empty(pinned.numel(), dtype=pinned.dtype, pin_memory=True) if pinned is not None else None
+        host = pinned.numpy().view(np.uint64) if pinned is not None else None
         host_out = out_pinned.numpy().view(np.uint64) if out_pinned is not None else None
         if layout == gol.GOL_LAYOUT_PACKED:
             # warm-up of the transfer path (staging buffers come from the caching allocator)
@@ -382,7 +551,7 @@ def run_gpu(args, rank, world, local):
         barrier()
         t0 = time.perf_counter()
         h2d = d2h = 0
-        phase = {"upload_s": 0.0, "step_s": 0.0, "download_s": 0.0}
+        phase = {"upload_ms": 0.0, "step_ms": 0.0, "download_ms": 0.0}
         for _ in range(e2e_steps):
             if layout == gol.GOL_LAYOUT_PACKED:
                 # one upload of all boards, the step, one download of all boards
@@ -397,9 +566,9 @@ def run_gpu(args, rank, world, local):
                 gol.gol_get_packed_batch(handle_array, host_out)
                 d2h += host_out.nbytes
                 td = time.perf_counter()
-                phase["upload_s"] += tb - ta
-                phase["step_s"] += tc - tb
-                phase["download_s"] += td - tc
+                phase["upload_ms"] += (tb - ta) * 1e3
+                phase["step_ms"] += (tc - tb) * 1e3
+                phase["download_ms"] += (td - tc) * 1e3
             else:
                 cells = [synth.bernoulli_board(s.rows, s.cols, s.density, s.seed) for s in specs]
                 for b, c in zip(boards, cells):
@@ -412,21 +581,14 @@ def run_gpu(args, rank, world, local):
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         e2e = {"value": total_cells_gens * world / e2e_s / 1e9, "unit": "GCUPS",
                "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
-               "ms_per_phase": {k: round(v / e2e_steps * 1e3, 3) for k, v in phase.items()}}
+               "ms_per_phase": {k: round(v / e2e_steps, 3) for k, v in phase.items()}}
 
     # ---- roofline of the dominant kernel (the persistent step kernel) ---------------
     ops = float("nan") if args.no_probe else gol.gol_probe_int_throughput()[0]
-    achieved_tops = total_words_gens * INT_OPS_PER_WORD_GEN / (min(step_ms) * 1e-3) / 1e12 \
+    rl = roofline(gol, total_words_gens, mean_ms, ops, args.workload) \
         if layout == gol.GOL_LAYOUT_PACKED else None
-    roofline = None
-    if achieved_tops is not None:
-        peak = ops / 1e12
-        roofline = {"bound": "alu", "achieved": round(achieved_tops, 3), "peak": round(peak, 3),
-                    "unit": "Tops/s", "frac": round(achieved_tops / peak, 4),
-                    "traffic": recorded_traffic(args.workload) if args.boards == 4096 or args.workload != "batch"
-                    else None,
-                    "peak_source": "integer-pipe probe (LOP3/funnel-shift mix) measured in this run",
-                    "algorithmic_ops_per_launch": total_words_gens * INT_OPS_PER_WORD_GEN}
+    if rl is not None and not (args.boards == 4096 or args.workload != "batch"):
+        rl["traffic"] = None
 
     out = {
         "metric": "GCUPS batched (gol_step_batch) vs plain per-board loop on 1 GB300",
@@ -438,8 +600,8 @@ def run_gpu(args, rank, world, local):
                    "l2": "working set (2 buffers per board) larger than L2" if total_cells_gens and
                    sum(s.rows * s.cols // 4 for s in specs) > dinfo["l2_bytes"] else "fits in L2",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "clocks": clocks,
-        "gpu_launches": 2 * args.steps,
+        "clocks": res["clocks"],
+        "gpu_launches": res["launches"],
         "step_ms": [round(x, 3) for x in step_ms],
     }
     if plain:
@@ -447,27 +609,38 @@ def run_gpu(args, rank, world, local):
         out["speedup_vs_plain"] = round(value / world / plain["value"], 2)
     if e2e:
         out["e2e"] = e2e
-    if roofline:
-        out["roofline"] = roofline
+    if rl:
+        out["roofline"] = rl
     for b in boards:
         b.close()
+    del pinned
+    if args.workload == "batch" and not args.no_sub:
+        # the single-board workloads, each timed on its own
+        out["single"] = sub_bench(gol, "single", min(args.steps, 5), min(args.warmup, 3), stream, local, ops)
+        out["huge"] = sub_bench(gol, "huge", min(args.steps, 3), 1, stream, local, ops)
     if args.workload == "batch" and args.serve_requests > 0:
-        out["served"] = served_run(gol, args.serve_requests, args.serve_load, value / world, 120 << 30,
-                                   args.fcfs_requests)
+        n = args.serve_requests
+        words = request_words(synth.request_stream(n, 1.0, seed=synth.SEED_SERVE))
+        cap = value / world
+        out["served"] = served_run(n, args.serve_load, cap, 120 << 30, words, fcfs=args.fcfs)
+        out["served_load_1"] = served_run(n, 1.0, cap, 120 << 30, words)
+        out["served_budget"] = served_run(n, args.serve_load, cap, 32 << 20, words)
+        out["served_budget"]["note"] = ("32 MiB budget: a few of the largest boards at a time, so requests wait "
+                                        "for memory (a 2 GB budget never binds at this load)")
         if args.serve_sweep:
             keys = ("offered_load", "budget_bytes", "requests", "p50_ms", "p99_ms", "mean_ms", "gcups",
-                    "max_active", "max_waiting", "peak_device_bytes")
-            sweep = []
-            for load, budget in ((0.3, 120 << 30), (0.7, 120 << 30), (1.0, 120 << 30), (0.7, 32 << 20)):
-                r = served_run(gol, args.serve_requests, load, value / world, budget, 0)
-                sweep.append({k: r[k] for k in keys if k in r})
-            out["served_sweep"] = sweep
+                    "max_active", "max_waiting", "peak_device_bytes", "device_busy")
+            out["served_sweep"] = [{k: r[k] for k in keys if k in r} for r in
+                                   (served_run(n, load, cap, 120 << 30, words) for load in (0.3, 0.5))]
+        del words
     gol.gol_set_allocator(None, None)
     if rank == 0:
         if not args.no_cpu:
             g, cores, desc = cpu_oracle_sample(specs, args.cpu_seconds, 1)
             out["cpu_baseline"] = {"value": round(g, 5), "unit": "GCUPS", "cores": cores, "kind": "oracle",
-                                   "sample": desc}
+                                   "sample": desc, "host": host_facts()}
+            if args.workload == "batch" and not args.no_cpu_configs:
+                out["cpu_baseline"]["configs"] = cpu_baselines()
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -234,3 +234,46 @@ def test_fcfs_baseline_matches(serve_mod):
     for j in jobs:
         want = oracle.run(oracle.unpack_words(j.words), j.gens)
         assert np.array_equal(oracle.unpack_words(j.result), want)
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_bench_stream_served_equals_alone_and_oracle(serve_mod):
+    """The request stream the bench serves (its seed, 2000 requests, sides
+    up to 8192, 10 to 1e5 generations), offered faster than the device
+    steps it and under a 32 MiB budget, so that requests wait for memory
+    and share ticks.  Every result equals the request stepped alone with
+    gol_step; every request of at most 1e8 cell updates, and a seeded
+    sample of 16 between 1e8 and 1e9, also equals the oracle."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_1209_4408_gb300 import gol
+
+    reqs = synth.request_stream(2000, 2000.0, seed=synth.SEED_SERVE)
+    with ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+        words = list(ex.map(lambda r: synth.bernoulli_words(r.rows, r.cols, r.density, r.seed), reqs))
+    jobs = [serve_mod.Job(r.index, r.arrival_s, r.rows, r.cols, r.gens, w) for r, w in zip(reqs, words)]
+    st = serve_mod.Server(budget_bytes=32 << 20, keep_results=True).run(jobs)
+    s = st.summary()
+    assert s["requests"] == len(jobs) and s["max_waiting"] > 0 and s["max_active"] > 1
+    assert s["peak_device_bytes"] <= 32 << 20
+    for j in jobs:
+        h = gol.gol_create_ex(j.rows, j.cols, True, gol.GOL_LAYOUT_PACKED)
+        gol.gol_set_packed(h, j.words)
+        gol.gol_step(h, j.gens)
+        alone = gol.gol_get_packed(h)
+        gol.gol_destroy(h)
+        assert np.array_equal(j.result, alone), "request %d differs alone and in the mix" % j.rid
+    small = [j for j in jobs if j.work <= 10 ** 8]
+    mid = [j for j in jobs if 10 ** 8 < j.work <= 10 ** 9]
+    sample = [mid[i] for i in np.random.default_rng(2024).permutation(len(mid))[:16]]
+    assert len(small) > 500 and len(sample) == 16
+
+    def oracle_equal(j):
+        want = oracle.run(oracle.unpack_words(j.words), j.gens)
+        return j.rid, bool(np.array_equal(oracle.unpack_words(j.result), want))
+
+    with ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+        bad = [rid for rid, ok in ex.map(oracle_equal, small + sample) if not ok]
+    assert not bad, "requests differing from the oracle: %s" % bad[:10]
