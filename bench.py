@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "single", "huge", "bytes", "decomposition"])
+                    choices=["batch", "single", "huge", "masked", "bytes", "decomposition"])
     ap.add_argument("--boards", type=int, default=4096)
     ap.add_argument("--plain-sample", type=int, default=64, help="boards timed in the plain loop")
     ap.add_argument("--no-e2e", action="store_true")
@@ -107,6 +107,10 @@ def workload_specs(workload: str, nboards: int, rank: int = 0):
         return ([synth.BoardSpec(0, 131072, 131072, 0.5, 1000, synth.SEED_HUGE_128K)],
                 "single 131072x131072 toroidal packed board (2 GiB per buffer), Bernoulli(0.5) with a "
                 "cleared 4096-row band holding a 64x64 glider lattice, 1000 generations")
+    if workload == "masked":
+        return ([synth.BoardSpec(0, 16383, 16383, 0.5, 2000, synth.SEED_MASKED)],
+                "single 16383x16383 toroidal packed board (neither side a multiple of 64: 256 words per row, "
+                "63 columns in the last), Bernoulli(0.5), 2000 generations")
     if workload == "bytes":
         return ([synth.BoardSpec(0, 256, 256, 0.3, 1000, synth.SEED_BYTES_256)],
                 "single 256x256 toroidal byte-per-cell board, Bernoulli(0.3), 1000 generations")
@@ -389,20 +393,22 @@ def device_bench(gol, specs, layout, steps, warmup, stream, local, barrier=None)
 
     pinned, boards = None, []
     if layout == gol.GOL_LAYOUT_PACKED:
-        nwords = sum(s.rows * s.cols // 64 for s in specs)
+        nwords = sum(s.rows * ((s.cols + 63) // 64) for s in specs)
         pinned = torch.empty(nwords, dtype=torch.int64, pin_memory=True)
         host = pinned.numpy().view(np.uint64)
         views = []
         off = 0
         for s in specs:
-            n = s.rows * s.cols // 64
-            views.append((s, host[off:off + n].reshape(s.rows, s.cols // 64)))
+            n = s.rows * ((s.cols + 63) // 64)
+            views.append((s, host[off:off + n].reshape(s.rows, (s.cols + 63) // 64)))
             off += n
 
         def fill(item):
             s, v = item
             if s.seed == synth.SEED_HUGE_128K:
                 synth.glider_band_words(s.rows, s.cols // 64, s.seed, synth.GliderBand(), out=v)
+            elif s.cols % 64:
+                v[:] = synth.pack_rows(synth.bernoulli_board(s.rows, s.cols, s.density, s.seed))
             elif s.density == 0.5:
                 synth.random_words(s.rows, s.cols // 64, s.seed, out=v)
             else:
@@ -451,7 +457,7 @@ def device_bench(gol, specs, layout, steps, warmup, stream, local, barrier=None)
     res = {"ms_total": t_start.elapsed_time(t_end), "step_ms": step_ms, "clocks": clk.summary(),
            "launches": launches, "handles": handle_array, "gens": gens_array,
            "cells_gens": sum(s.rows * s.cols * s.gens for s in specs),
-           "words_gens": sum(s.rows * (s.cols // 64) * s.gens for s in specs)}
+           "words_gens": sum(s.rows * ((s.cols + 63) // 64) * s.gens for s in specs)}
     return res, boards, pinned
 
 
@@ -464,6 +470,25 @@ def roofline(gol, words_gens, mean_ms, peak_ops, workload):
             "peak_source": "integer-pipe probe (LOP3/funnel-shift mix) measured in this run",
             "algorithmic_ops_per_launch": words_gens * INT_OPS_PER_WORD_GEN,
             "time": "mean step (CUDA events on the launching stream)"}
+
+
+def byte_layout_gcups(gol, s, gens):
+    """The same board stored one byte per cell (the path such boards took
+    before they could be packed), `gens` generations timed after one."""
+    import torch
+
+    b = gol.Board(s.rows, s.cols, torus=True, layout=gol.GOL_LAYOUT_BYTES)
+    b.set(synth.bernoulli_board(s.rows, s.cols, s.density, s.seed))
+    b.step(1)
+    b.sync()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    b.step(gens)
+    e.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e)
+    b.close()
+    return round(s.rows * s.cols * gens / (ms * 1e-3) / 1e9, 2)
 
 
 def sub_bench(gol, workload, steps, warmup, stream, local, peak_ops):
@@ -480,6 +505,10 @@ def sub_bench(gol, workload, steps, warmup, stream, local, peak_ops):
            "roofline": roofline(gol, res["words_gens"], mean, peak_ops, workload)}
     for b in boards:
         b.close()
+    if workload == "masked":
+        out["byte_layout_gcups"] = byte_layout_gcups(gol, specs[0], 20)
+        out["note"] = ("roofline counts the 22 operations of a whole word; the masked last word adds 5 per word and "
+                       "stage; byte_layout_gcups: the same board one byte per cell, 20 generations")
     return out
 
 
@@ -589,6 +618,30 @@ def run_gpu(args, rank, world, local):
         if layout == gol.GOL_LAYOUT_PACKED else None
     if rl is not None and not (args.boards == 4096 or args.workload != "batch"):
         rl["traffic"] = None
+    # the per-class tune table against the library defaults, on the same boards
+    tune = None
+    if args.workload == "batch" and not args.no_sub:
+        def mean_ms(steps=3):
+            for _ in range(2):
+                step()
+            torch.cuda.synchronize()
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                step()
+            e.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(e) / steps
+
+        gol.gol_tune_reset()
+        default_ms = mean_ms()
+        from paper_1209_4408_gb300 import autotune
+
+        autotune.load_shipped()
+        tuned_ms = mean_ms()
+        tune = {"tuned_ms": round(tuned_ms, 3), "default_ms": round(default_ms, 3),
+                "gain": round(default_ms / tuned_ms, 4),
+                "table": "tune_gb300.json (per-class entries from autotune.tune_batch) vs no entries"}
 
     out = {
         "metric": "GCUPS batched (gol_step_batch) vs plain per-board loop on 1 GB300",
@@ -611,6 +664,8 @@ def run_gpu(args, rank, world, local):
         out["e2e"] = e2e
     if rl:
         out["roofline"] = rl
+    if tune:
+        out["autotune"] = tune
     for b in boards:
         b.close()
     del pinned
@@ -618,6 +673,7 @@ def run_gpu(args, rank, world, local):
         # the single-board workloads, each timed on its own
         out["single"] = sub_bench(gol, "single", min(args.steps, 5), min(args.warmup, 3), stream, local, ops)
         out["huge"] = sub_bench(gol, "huge", min(args.steps, 3), 1, stream, local, ops)
+        out["masked"] = sub_bench(gol, "masked", min(args.steps, 5), min(args.warmup, 2), stream, local, ops)
     if args.workload == "batch" and args.serve_requests > 0:
         n = args.serve_requests
         words = request_words(synth.request_stream(n, 1.0, seed=synth.SEED_SERVE))

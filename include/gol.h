@@ -42,8 +42,9 @@ extern "C" {
 #define GOL_EBUSY (-5)    /* reserved; not returned: calls are serialised and stream-ordered      */
 
 /* Board storage chosen at creation. */
-#define GOL_LAYOUT_AUTO 0   /* packed when cols % 64 == 0 or rows % 64 == 0, else bytes         */
-#define GOL_LAYOUT_PACKED 1 /* 64 cells per uint64 (cols % 64 == 0 or rows % 64 == 0 required)    */
+#define GOL_LAYOUT_AUTO 0   /* packed, except a board with neither side a multiple of 64 whose     */
+                            /* cells fit one thread-block cluster's shared memory: bytes           */
+#define GOL_LAYOUT_PACKED 1 /* 64 cells per uint64, any rows, cols >= 1                            */
 #define GOL_LAYOUT_BYTES 2  /* one uint8 per cell, any rows, cols >= 1                            */
 
 typedef struct gol_board *gol_handle;
@@ -55,12 +56,19 @@ typedef struct gol_board *gol_handle;
  * for sizes < 1 or a null `out`, GOL_ENOMEM, GOL_ECUDA. */
 int gol_create(int64_t rows, int64_t cols, int torus, gol_handle *out);
 
-/* As gol_create with an explicit layout (GOL_LAYOUT_*).  GOL_LAYOUT_PACKED
- * needs cols % 64 == 0 or rows % 64 == 0 (else GOL_EINVAL).  A packed board
- * whose width is not a multiple of 64 is stored transposed (words along the
- * height); it steps like any packed board, but has no packed word layout:
- * gol_set_packed / gol_get_packed (and their device and batch forms) are
- * GOL_EINVAL for it, gol_set / gol_get / gol_get_region work. */
+/* As gol_create with an explicit layout (GOL_LAYOUT_*).  Packed boards:
+ *   - cols % 64 == 0: cols/64 words per row (stored transposed when that
+ *     fills the warps better; the interchange layout is the same);
+ *   - cols % 64 != 0, rows % 64 == 0: stored transposed (words along the
+ *     height); it steps like any packed board, but has no packed word
+ *     layout: gol_set_packed / gol_get_packed (and their device and batch
+ *     forms) are GOL_EINVAL for it, gol_set / gol_get / gol_get_region work;
+ *   - neither a multiple of 64: ceil(cols/64) words per row, the last one
+ *     holding cols % 64 columns in its low bits (masked last word); its
+ *     packed word layout has ceil(cols/64) words per row, padding bits are
+ *     ignored on input and zero on output.  The step kernel carries the
+ *     wrap across the partial word (a few more integer operations per word
+ *     than a whole-word board). */
 int gol_create_ex(int64_t rows, int64_t cols, int torus, int layout, gol_handle *out);
 
 /* Releases the board.  The handle is invalid on return; the device memory
@@ -80,9 +88,10 @@ int gol_set(gol_handle h, const uint8_t *cells, size_t n);
  * Synchronises the stream first. */
 int gol_get(gol_handle h, uint8_t *cells, size_t n);
 
-/* Packed variants: `words` is host memory of nwords == rows*cols/64 words
- * in the packed layout.  Only for packed boards (else GOL_EINVAL).
- * gol_set_packed resets the generation counter. */
+/* Packed variants: `words` is host memory of nwords == rows*ceil(cols/64)
+ * words in the packed layout.  Only for packed boards that have a word
+ * layout (else GOL_EINVAL; see gol_create_ex).  gol_set_packed resets the
+ * generation counter. */
 int gol_set_packed(gol_handle h, const uint64_t *words, size_t nwords);
 int gol_get_packed(gol_handle h, uint64_t *words, size_t nwords);
 
@@ -159,10 +168,23 @@ int gol_step_batch(const gol_handle *hs, const int64_t *generations, size_t n);
  * Synchronous. */
 int gol_population(gol_handle h, uint64_t *out);
 
-/* Population trajectory (the form of the paper's Table 1): advances the
- * board n times by `every` generations (every >= 1) and writes the number of
- * live cells after each advance to host out[0..n).  Synchronous. */
+/* Population trajectory (the form of the paper's Table 1, Section 3.1):
+ * advances the board n times by `every` generations (every >= 1) and writes
+ * the number of live cells after each advance to host out[0..n).  As
+ * gol_population_trace_batch with one board.  Synchronous. */
 int gol_population_trace(gol_handle h, int64_t every, size_t n, uint64_t *out);
+
+/* Population trajectories of several boards at once: advances every board
+ * hs[i] (distinct handles) by samples x every generations and writes its
+ * number of live cells after each `every` generations to host
+ * out[i * samples + k], k = 0 .. samples - 1.  Packed boards are stepped in
+ * one persistent launch per torus flag (and per 2^24 generations), with
+ * their passes aligned to the sampling period: at the end of each period
+ * the step kernel adds up the live cells of the words it has just written.
+ * Byte boards, and periods longer than 2^24 generations, are stepped and
+ * counted sample by sample.  Synchronous.  GOL_EINVAL for null pointers,
+ * every < 1, repeated or invalid handles. */
+int gol_population_trace_batch(const gol_handle *hs, size_t n, int64_t every, size_t samples, uint64_t *out);
 
 /* Generations applied since the last gol_set / gol_set_packed. */
 int gol_generation(gol_handle h, int64_t *out);
@@ -259,6 +281,19 @@ int gol_tune_set(int64_t rows, int64_t cols, int gens_per_pass, int tile_rows);
 int gol_tune_get(int64_t rows, int64_t cols, int *gens_per_pass, int *tile_rows);
 /* Removes every entry of the autotune table (built-in defaults apply). */
 int gol_tune_reset(void);
+
+/* The autotune table's class of a rows x cols board (host only):
+ * *row_class = ceil(log2(rows)), *word_class = ceil(cols/64) when at most 32
+ * words, else 32 + ceil(log2(words)).  Boards are looked up by their stored
+ * shape (gol_board_storage), so a board stored transposed uses the class of
+ * cols x rows. */
+int gol_tune_class(int64_t rows, int64_t cols, int *row_class, int *word_class);
+
+/* How a board is stored on the device (host only): *srows stored rows of
+ * *swords words (packed boards; a byte board reports rows and 0 words),
+ * *transposed = 1 when stored row c holds board column c.  Any output
+ * pointer may be null. */
+int gol_board_storage(gol_handle h, int64_t *srows, int64_t *swords, int *transposed);
 
 /* Unit plan of a packed step (host only, no device needed).  Describes the
  * units a persistent launch uses for one board stored as `rows` x `words`

@@ -72,6 +72,109 @@ def tune_shape(rows: int, cols: int, gens: int = 256, ks=DEFAULT_K, tile_rows=DE
             "trials": [(round(rows * cols / t / 1e9, 2), kk, rr) for t, kk, rr in trials]}
 
 
+def _time_batch(handles: np.ndarray, gens: np.ndarray, steps: int, warmup: int) -> float:
+    """Mean seconds of one gol_step_batch of the boards (CUDA events on the
+    library's stream, which must be PyTorch's current stream)."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        gol.gol_step_batch(handles, gens)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        gol.gol_step_batch(handles, gens)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) * 1e-3 / steps
+
+
+def batch_classes(handles, gens) -> list:
+    """Size classes of the packed boards of a batch, most work first: dicts
+    with the class key, a representative stored shape (rows, cols) for
+    gol_tune_set, the class's share of the batch's cell updates and its
+    boards' largest generation count."""
+    classes = {}
+    total = 0
+    for h, g in zip(handles, gens):
+        srows, swords, _ = gol.gol_board_storage(int(h))
+        if swords == 0:
+            continue
+        key = gol.gol_tune_class(srows, swords * 64)
+        work = srows * swords * 64 * int(g)
+        total += work
+        c = classes.setdefault(key, {"key": key, "rows": srows, "cols": swords * 64, "work": 0, "boards": 0,
+                                     "max_gens": 0})
+        c["work"] += work
+        c["boards"] += 1
+        c["max_gens"] = max(c["max_gens"], int(g))
+    out = sorted(classes.values(), key=lambda c: -c["work"])
+    for c in out:
+        c["share"] = c["work"] / max(1, total)
+    return out
+
+
+def tune_batch(handles, gens, classes: int = 12, tile_rows=(24, 32, 48, 64, 96, 128, 192, 256),
+               ks=(5, 6, 7), steps: int = 4, warmup: int = 2, min_gain: float = 0.003) -> dict:
+    """Tunes the size classes of one batch on the batch itself.  The
+    planner takes the generations per pass of a launch from the board with
+    the most work and each board's tile rows from its class's entry (then
+    shortens the units of boards with long chains), so a class's best tile
+    height depends on the rest of the batch: each of the `classes` classes
+    with the most work gets, in turn, the tile height that makes the whole
+    batch fastest with the others fixed (coordinate descent), then the
+    class that sets the launch's generations per pass tries each K in
+    `ks`.  A trial replaces the incumbent only when it is faster by more
+    than `min_gain` (timing noise).  Installs the entries found
+    (gol_tune_set) and returns them with the batch time before and after."""
+    handles = np.ascontiguousarray(handles, dtype=np.uint64)
+    gens = np.ascontiguousarray(gens, dtype=np.int64)
+    cls = batch_classes(handles, gens)[:classes]
+    before = _time_batch(handles, gens, steps, warmup)
+    entries = {}
+    for c in cls:
+        k0, r0 = gol.gol_tune_get(c["rows"], c["cols"])
+        entries[c["key"]] = [k0, r0]
+    best_t = before
+    for c in cls:
+        k, r_best = entries[c["key"]]
+        for tr in tile_rows:
+            if tr == r_best:
+                continue
+            gol.gol_tune_set(c["rows"], c["cols"], k, tr)
+            t = _time_batch(handles, gens, steps, warmup)
+            if t < best_t * (1 - min_gain):
+                best_t, r_best = t, tr
+        gol.gol_tune_set(c["rows"], c["cols"], k, r_best)
+        entries[c["key"]] = [k, r_best]
+    # generations per pass: the launch takes the K of the board with the most work
+    lead = max(zip(handles, gens), key=lambda hg: gol.gol_board_storage(int(hg[0]))[0] *
+               gol.gol_board_storage(int(hg[0]))[1] * int(hg[1]))
+    srows, swords, _ = gol.gol_board_storage(int(lead[0]))
+    k_best, r_lead = gol.gol_tune_get(srows, swords * 64)
+    for k in ks:
+        if k == k_best:
+            continue
+        for c in cls:                        # the same K for every tuned class keeps one K per launch
+            gol.gol_tune_set(c["rows"], c["cols"], k, entries[c["key"]][1])
+        gol.gol_tune_set(srows, swords * 64, k, r_lead)
+        t = _time_batch(handles, gens, steps, warmup)
+        if t < best_t * (1 - min_gain):
+            best_t, k_best = t, k
+    for c in cls:
+        gol.gol_tune_set(c["rows"], c["cols"], k_best, entries[c["key"]][1])
+        entries[c["key"]][0] = k_best
+    gol.gol_tune_set(srows, swords * 64, k_best, r_lead)
+    after = _time_batch(handles, gens, steps, warmup)
+    out = []
+    for c in cls:
+        out.append({"rows": c["rows"], "cols": c["cols"], "k": entries[c["key"]][0],
+                    "tile_rows": entries[c["key"]][1], "class": list(c["key"]), "share": round(c["share"], 4),
+                    "boards": c["boards"]})
+    return {"entries": out, "before_s": before, "after_s": after, "lead": [int(srows), int(swords * 64)]}
+
+
 def save(entries: list, path: str | None = None):
     path = path or cache_path()
     os.makedirs(os.path.dirname(path), exist_ok=True)

@@ -41,6 +41,12 @@ struct gol_board {
     // be) is always stored transposed, so that its stored rows are whole
     // words; it has no packed interchange layout (words = 0).
     int odd_width = 0;
+    // A packed board with neither side a multiple of 64 keeps its rows as
+    // ceil(cols / 64) words, the last word holding last_bits columns and zero
+    // padding (see the masked variant of the step kernel).  Its packed
+    // interchange layout has that many words per row as well.
+    int masked = 0;
+    int last_bits = 0;
     // byte boards: captured graphs of 64 generations, per starting buffer
     cudaGraphExec_t byte_graph[2] = {nullptr, nullptr};
     cudaStream_t byte_graph_stream = nullptr;
@@ -214,6 +220,12 @@ struct Plan {
     bool torus = true;
     int64_t opt_k = 0, opt_rows = 0, opt_chain = 0, opt_variant = 0, opt_critical = 0;
     int variant = 0;
+    // population trace: every board's generation count is a whole number of
+    // sampling periods of `every` generations; pop_first[i] is board i's
+    // first sample slot (0 = no trace)
+    int64_t every = 0;
+    std::vector<int32_t> pop_first;
+    bool masked = false;   // the boards have a masked last word (one launch holds only such boards or none)
     // host copies
     std::vector<BoardDesc> boards;
     std::vector<UnitDesc> units;
@@ -308,8 +320,11 @@ UnitGrid unit_grid(int64_t rows, int64_t words, int K, int tile_rows) {
 }
 
 // Writes the g.nb * g.nt units of a board to out[0..); unit ids are
-// first + index.  Uses no dynamic memory.
-void fill_units(int64_t rows, int64_t words, int bindex, const UnitGrid &g, UnitDesc *out, int first) {
+// first + index.  `seam` > 0 rotates the word tiles by that many words
+// (tile 0 starts at word W - seam and wraps), so that on a torus whose
+// last word is partial that word and word 0 are output words of one tile
+// rather than another tile's halo words.  Uses no dynamic memory.
+void fill_units(int64_t rows, int64_t words, int bindex, const UnitGrid &g, UnitDesc *out, int first, int seam = 0) {
     const int R = (int)rows, W = (int)words, nb = g.nb, nt = g.nt, S = g.S;
     for (int i = 0; i < nb; ++i) {
         const int r0 = (int)((int64_t)R * i / nb), r1 = (int)((int64_t)R * (i + 1) / nb);
@@ -329,8 +344,9 @@ void fill_units(int64_t rows, int64_t words, int bindex, const UnitGrid &g, Unit
                 u.mode = kUnitTiled;
                 u.H = bh;
                 u.S = 1;
-                u.w0 = (int)((int64_t)W * t / nt);
-                u.U = (int)((int64_t)W * (t + 1) / nt) - u.w0;
+                const int lo = (int)((int64_t)W * t / nt);
+                u.U = (int)((int64_t)W * (t + 1) / nt) - lo;
+                u.w0 = (lo + W - seam) % W;
             }
             // neighbours: adjacent row blocks x adjacent tiles (wrapping), minus self
             u.nnb = 0;
@@ -398,7 +414,11 @@ void build_units(const gol_board *h, int bindex, int K, int tile_rows, std::vect
     const UnitGrid g = unit_grid(h->srows, h->swords, K, tile_rows);
     const size_t first = units.size();
     units.resize(first + (size_t)g.nb * g.nt);
-    fill_units(h->srows, h->swords, bindex, g, units.data() + first, (int)first);
+    // a tiled torus with a partial last word: that word and word 0 in the
+    // middle of tile 0 (a halo word must hold K valid columns beyond the
+    // tile, the partial word may hold fewer)
+    const int seam = (h->masked && h->torus && !g.full) ? (int)(h->swords / g.nt) / 2 : 0;
+    fill_units(h->srows, h->swords, bindex, g, units.data() + first, (int)first, seam);
     set_board_cost(units.data() + first, g.nb * g.nt, K);
     *nunits_out = g.nb * g.nt;
 }
@@ -448,6 +468,14 @@ double board_row_work(int64_t srows, int64_t swords, int64_t npass) {
     return (double)npass * (double)((srows + S - 1) / S) * (double)nt;
 }
 
+// Passes of board i in a launch: its generations in passes of at most K,
+// or, in a population trace, each sampling period of `every` generations in
+// ceil(every / K) passes.
+int64_t plan_npass(const Plan &P, size_t i) {
+    if (P.every > 0) return (P.gens[i] / P.every) * ((P.every + P.K - 1) / P.K);
+    return (P.gens[i] + P.K - 1) / P.K;
+}
+
 int build_plan(Plan &P) {
     const size_t n = P.hs.size();
     P.boards.clear();
@@ -464,13 +492,17 @@ int build_plan(Plan &P) {
         }
     }
     P.K = supported_k(std::max(1, K));
+    // boards with a masked last word and population traces run kernel
+    // variants 4 / 5 / 6, which exist for 4, 6 and 8 generations per pass
+    P.masked = P.hs[0]->masked != 0;
+    if (P.masked || P.every > 0) P.K = P.K >= 8 ? 8 : (P.K >= 6 ? 6 : 4);
     int64_t units_estimate = 0;    // with the tuned tile rows, before any chain cap
     for (size_t i = 0; i < n; ++i) {
         const UnitGrid ug = unit_grid(P.hs[i]->srows, P.hs[i]->swords, P.K,
                                       std::max(1, tune_lookup(P.hs[i]->srows, P.hs[i]->swords * 64).rows));
         units_estimate += (int64_t)ug.nb * ug.nt;
     }
-    P.variant = plan_variant(P.K, units_estimate);
+    P.variant = P.masked ? (P.every > 0 ? 6 : 4) : (P.every > 0 ? 5 : plan_variant(P.K, units_estimate));
     int bps = 1;
     cudaError_t e = occupancy_for(P.K, P.torus, P.variant, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -485,11 +517,11 @@ int build_plan(Plan &P) {
     for (size_t i = 0; i < n; ++i) {
         const gol_board *h = P.hs[i];
         hrows[i] = std::max(1, tune_lookup(h->srows, h->swords * 64).rows);
-        work += board_row_work(h->srows, h->swords, (P.gens[i] + P.K - 1) / P.K);
+        work += board_row_work(h->srows, h->swords, plan_npass(P, i));
     }
     const double chain_cap = g_opt_rows ? 1e300 : chain_fraction(n) * work / (double)slots;
     for (size_t i = 0; i < n; ++i)
-        hrows[i] = capped_tile_rows(hrows[i], (P.gens[i] + P.K - 1) / P.K, P.K, chain_cap);
+        hrows[i] = capped_tile_rows(hrows[i], plan_npass(P, i), P.K, chain_cap);
     P.total_tasks = 0;
     P.boards.resize(n);
     P.npass.resize(n);
@@ -498,8 +530,8 @@ int build_plan(Plan &P) {
     std::vector<size_t> order(n);
     for (size_t i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
-        const double cx = (double)((P.gens[x] + P.K - 1) / P.K) * hrows[x];
-        const double cy = (double)((P.gens[y] + P.K - 1) / P.K) * hrows[y];
+        const double cx = (double)plan_npass(P, x) * hrows[x];
+        const double cy = (double)plan_npass(P, y) * hrows[y];
         return cx > cy;
     });
     for (size_t i : order) {
@@ -511,7 +543,10 @@ int build_plan(Plan &P) {
         bd.R = (int32_t)h->srows;
         bd.W = (int32_t)h->swords;
         bd.gens = (int32_t)P.gens[i];
-        bd.npass = (int32_t)((P.gens[i] + P.K - 1) / P.K);
+        bd.npass = (int32_t)plan_npass(P, i);
+        bd.ppp = P.every > 0 ? (int32_t)((P.every + P.K - 1) / P.K) : 0;
+        bd.pop_off = P.every > 0 ? P.pop_first[i] : 0;
+        bd.last_bits = h->last_bits;
         build_units(h, (int)i, P.K, hrows[i], P.units, &bd.nunits);
         P.total_tasks += (int64_t)bd.nunits * bd.npass;
         P.boards[i] = bd;
@@ -852,12 +887,13 @@ int gol_create_ex(int64_t rows, int64_t cols, int torus, int layout, gol_handle 
     *out = nullptr;
     if (rows < 1 || cols < 1) return fail(GOL_EINVAL, "rows and cols must be >= 1 (got %lld x %lld)",
                                           (long long)rows, (long long)cols);
+    // a board with neither side a multiple of 64 is bytes when its cells fit
+    // one thread-block cluster (all generations in one launch), else packed
+    // with a masked last word
     if (layout == GOL_LAYOUT_AUTO)
-        layout = (cols % 64 == 0 || rows % 64 == 0) ? GOL_LAYOUT_PACKED : GOL_LAYOUT_BYTES;
+        layout = (cols % 64 == 0 || rows % 64 == 0 || byte_cluster_size(rows, cols) == 0) ? GOL_LAYOUT_PACKED
+                                                                                         : GOL_LAYOUT_BYTES;
     if (layout != GOL_LAYOUT_PACKED && layout != GOL_LAYOUT_BYTES) return fail(GOL_EINVAL, "unknown layout %d", layout);
-    if (layout == GOL_LAYOUT_PACKED && cols % 64 != 0 && rows % 64 != 0)
-        return fail(GOL_EINVAL, "packed layout needs cols or rows a multiple of 64 (%lld x %lld)", (long long)rows,
-                    (long long)cols);
     if (layout == GOL_LAYOUT_PACKED && (rows > (int64_t(1) << 30) || cols > (int64_t(1) << 30)))
         return fail(GOL_EINVAL, "board too large");
     int rc = ensure_device();
@@ -868,9 +904,13 @@ int gol_create_ex(int64_t rows, int64_t cols, int torus, int layout, gol_handle 
     h->cols = cols;
     h->torus = torus ? 1 : 0;
     h->layout = layout;
-    h->odd_width = layout == GOL_LAYOUT_PACKED && cols % 64 != 0;
-    h->words = layout == GOL_LAYOUT_PACKED && !h->odd_width ? cols / 64 : 0;
-    h->buf_bytes = layout == GOL_LAYOUT_PACKED ? (size_t)rows * (size_t)cols / 8 : (size_t)rows * (size_t)cols;
+    h->masked = layout == GOL_LAYOUT_PACKED && cols % 64 != 0 && rows % 64 != 0;
+    h->last_bits = h->masked ? (int)(cols % 64) : 0;
+    h->odd_width = layout == GOL_LAYOUT_PACKED && cols % 64 != 0 && !h->masked;
+    h->words = layout == GOL_LAYOUT_PACKED && !h->odd_width ? (cols + 63) / 64 : 0;
+    h->buf_bytes = layout == GOL_LAYOUT_PACKED ? (h->masked ? (size_t)rows * (size_t)h->words * 8
+                                                            : (size_t)rows * (size_t)cols / 8)
+                                               : (size_t)rows * (size_t)cols;
     h->alloc_fn = g_alloc;
     h->free_fn = g_free;
     h->alloc_ctx = g_alloc_ctx;
@@ -881,7 +921,7 @@ int gol_create_ex(int64_t rows, int64_t cols, int torus, int layout, gol_handle 
         h->transposed = 1;
         h->srows = cols;
         h->swords = rows / 64;
-    } else if (layout == GOL_LAYOUT_PACKED && rows % 64 == 0 && g_opt_orient != 1) {
+    } else if (layout == GOL_LAYOUT_PACKED && !h->masked && rows % 64 == 0 && g_opt_orient != 1) {
         bool t = g_opt_orient == 2;
         if (!t) {
             const TuneEntry a = tune_lookup(rows, cols), b = tune_lookup(cols, rows);
@@ -974,6 +1014,10 @@ int gol_set(gol_handle h, const uint8_t *cells, size_t n) {
         CU(cudaMemcpyAsync(st.p, cells, n, cudaMemcpyHostToDevice, g_stream));
         if (h->odd_width) {
             CU(launch_pack_transposed((const uint8_t *)st.p, h->rows, h->cols, (uint64_t *)h->buf[0], bad, g_stream));
+        } else if (h->masked) {
+            CU(launch_pack_rows((const uint8_t *)st.p, (uint64_t *)h->buf[1], h->rows, h->cols, bad, g_stream));
+            CU(launch_orient((const uint64_t *)h->buf[1], (uint64_t *)h->buf[0], h->rows, h->words, false, true,
+                             g_stream, h->last_bits));
         } else {
             CU(launch_pack((const uint8_t *)st.p, (uint64_t *)h->buf[1], h->rows, h->words, bad, g_stream));
             CU(launch_orient((const uint64_t *)h->buf[1], (uint64_t *)h->buf[0], h->rows, h->words, h->transposed,
@@ -999,10 +1043,15 @@ int gol_get(gol_handle h, uint8_t *cells, size_t n) {
         return sync_stream();
     }
     const size_t woff = (n + 255) & ~size_t(255);
-    Scratch st(woff + n / 8);
+    Scratch st(woff + (size_t)h->rows * (size_t)((h->cols + 63) / 64) * 8);
     if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", n);
     if (h->odd_width) {
         CU(launch_unpack_transposed((const uint64_t *)h->buf[h->cur], h->rows, h->cols, (uint8_t *)st.p, g_stream));
+    } else if (h->masked) {
+        uint64_t *words = (uint64_t *)((char *)st.p + woff);
+        CU(launch_orient((const uint64_t *)h->buf[h->cur], words, h->rows, h->words, false, false, g_stream,
+                         h->last_bits));
+        CU(launch_unpack_rows(words, (uint8_t *)st.p, h->rows, h->cols, g_stream));
     } else {
         uint64_t *words = (uint64_t *)((char *)st.p + woff);
         CU(launch_orient((const uint64_t *)h->buf[h->cur], words, h->rows, h->words, h->transposed, false,
@@ -1024,7 +1073,7 @@ int gol_set_packed(gol_handle h, const uint64_t *words, size_t nwords) {
     h->generation = 0;
     CU(cudaMemcpyAsync(h->buf[1], words, nwords * 8, cudaMemcpyHostToDevice, g_stream));
     CU(launch_orient((const uint64_t *)h->buf[1], (uint64_t *)h->buf[0], h->rows, h->words, h->transposed, true,
-                     g_stream));
+                     g_stream, h->last_bits));
     return set_cur_device(h);
 }
 
@@ -1038,7 +1087,7 @@ int gol_get_packed(gol_handle h, uint64_t *words, size_t nwords) {
     Scratch st(nwords * 8);
     if (!st.p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", nwords * 8);
     CU(launch_orient((const uint64_t *)h->buf[h->cur], (uint64_t *)st.p, h->rows, h->words, h->transposed, false,
-                     g_stream));
+                     g_stream, h->last_bits));
     CU(cudaMemcpyAsync(words, st.p, nwords * 8, cudaMemcpyDeviceToHost, g_stream));
     return sync_stream();
 }
@@ -1053,7 +1102,8 @@ int gol_set_packed_device(gol_handle h, const uint64_t *dwords, size_t nwords) {
     h->cur = 0;
     h->generation = 0;
     if (dwords == h->buf[0] || dwords == h->buf[1]) return fail(GOL_EINVAL, "source is the board's own buffer");
-    CU(launch_orient(dwords, (uint64_t *)h->buf[0], h->rows, h->words, h->transposed, true, g_stream));
+    CU(launch_orient(dwords, (uint64_t *)h->buf[0], h->rows, h->words, h->transposed, true, g_stream,
+                     h->last_bits));
     return set_cur_device(h);
 }
 
@@ -1064,7 +1114,8 @@ int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords) {
     if (h->odd_width) return fail(GOL_EINVAL, "a board %lld cells wide has no packed word layout", (long long)h->cols);
     if (nwords != (size_t)(h->rows * h->words))
         return fail(GOL_EINVAL, "nwords = %zu, board has %lld words", nwords, (long long)(h->rows * h->words));
-    CU(launch_orient((const uint64_t *)h->buf[h->cur], dwords, h->rows, h->words, h->transposed, false, g_stream));
+    CU(launch_orient((const uint64_t *)h->buf[h->cur], dwords, h->rows, h->words, h->transposed, false, g_stream,
+                     h->last_bits));
     return GOL_OK;
 }
 
@@ -1137,7 +1188,7 @@ int copy_plan(const gol_handle *hs, size_t n, const CopyPlan **out) {
         d[i].rows = h->rows;
         d[i].words = h->words;
         d[i].transposed = h->transposed;
-        d[i].pad = 0;
+        d[i].last_bits = h->last_bits;
         d[i].block0 = P->blocks;
         P->transposed = P->transposed || h->transposed;
         const int64_t nb = copy_blocks(d[i]);
@@ -1262,25 +1313,105 @@ int gol_step_batch(const gol_handle *hs, const int64_t *generations, size_t n) {
     return step_batch_locked(hs, generations, n);
 }
 
+namespace {
+// One launch of a population trace: packed boards `hs` (one torus flag),
+// board i advanced by gens[i], a whole number of periods of `every`
+// generations; the step kernel adds the live cells of every unit at the end
+// of each period into pop[pop_first[i] + period].  The plan is built for
+// this launch alone (its sample slots are this call's) and freed once the
+// launch has run.
+int run_packed_trace(const std::vector<gol_handle> &hs, const std::vector<int64_t> &gens, bool torus, int64_t every,
+                     const std::vector<int32_t> &pop_first, unsigned long long *pop) {
+    auto P = std::make_unique<Plan>();
+    P->hs = hs;
+    P->gens = gens;
+    P->torus = torus;
+    P->every = every;
+    P->pop_first = pop_first;
+    for (auto h : hs) P->serials.push_back(h->serial);
+    int rc = build_plan(*P);
+    if (rc) return rc;
+    P->args.pop = pop;
+    cudaError_t e = launch_plan_kernels(*P, g_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launching a population trace");
+    for (size_t i = 0; i < hs.size(); ++i) {
+        hs[i]->cur ^= (P->npass[i] & 1);
+        hs[i]->generation += gens[i];
+    }
+    bury(std::move(P));
+    return GOL_OK;
+}
+
+int step_batch_locked(const gol_handle *hs, const int64_t *generations, size_t n);
+
+int population_trace_locked(const gol_handle *hs, size_t n, int64_t every, size_t samples, uint64_t *out) {
+    if (n == 0 || samples == 0) return GOL_OK;
+    if (!hs || !out) return fail(GOL_EINVAL, "null handles or output");
+    if (every < 1) return fail(GOL_EINVAL, "every must be >= 1");
+    if (samples > ((size_t)1 << 30) / n) return fail(GOL_EINVAL, "too many samples (%zu x %zu)", n, samples);
+    const uint64_t stamp = ++g_batch_stamp;
+    for (size_t i = 0; i < n; ++i) {
+        if (!valid(hs[i])) return fail(GOL_EINVAL, "invalid handle at %zu", i);
+        if (hs[i]->batch_stamp == stamp) return fail(GOL_EINVAL, "handle repeated at %zu", i);
+        hs[i]->batch_stamp = stamp;
+    }
+    Scratch st(n * samples * sizeof(unsigned long long));
+    if (!st.p) return fail(GOL_ENOMEM, "population trace slots");
+    unsigned long long *slots = (unsigned long long *)st.p;
+    CU(cudaMemsetAsync(slots, 0, n * samples * sizeof(unsigned long long), g_stream));
+    // byte boards, and any board whose period is longer than one launch:
+    // advanced and counted sample by sample
+    for (size_t i = 0; i < n; ++i) {
+        gol_handle h = hs[i];
+        if (h->layout == GOL_LAYOUT_PACKED && every <= kMaxGensPerLaunch) continue;
+        for (size_t k = 0; k < samples; ++k) {
+            int rc = step_batch_locked(&h, &every, 1);
+            if (rc) return rc;
+            if (h->layout == GOL_LAYOUT_PACKED)
+                CU(launch_popcount_packed((const uint64_t *)h->buf[h->cur], h->srows * h->swords,
+                                          slots + i * samples + k, g_stream));
+            else
+                CU(launch_popcount_bytes((const uint8_t *)h->buf[h->cur], h->rows * h->cols,
+                                         slots + i * samples + k, g_stream));
+        }
+    }
+    // packed boards: counted inside the step kernel, one launch per torus
+    // flag and run of whole periods
+    if (every <= kMaxGensPerLaunch) {
+        const size_t per = (size_t)std::max<int64_t>(1, kMaxGensPerLaunch / every);
+        for (int group = 0; group < 4; ++group) {
+            const int torus = group < 2 ? 1 : 0, masked = group & 1;
+            std::vector<gol_handle> grp;
+            std::vector<size_t> idx;
+            for (size_t i = 0; i < n; ++i)
+                if (hs[i]->layout == GOL_LAYOUT_PACKED && hs[i]->torus == torus && hs[i]->masked == masked) {
+                    grp.push_back(hs[i]);
+                    idx.push_back(i);
+                }
+            for (size_t s0 = 0; s0 < samples && !grp.empty(); s0 += per) {
+                const size_t m = std::min(per, samples - s0);
+                std::vector<int64_t> g(grp.size(), (int64_t)m * every);
+                std::vector<int32_t> first(grp.size());
+                for (size_t j = 0; j < grp.size(); ++j) first[j] = (int32_t)(idx[j] * samples + s0);
+                int rc = run_packed_trace(grp, g, torus == 1, every, first, slots);
+                if (rc) return rc;
+            }
+        }
+    }
+    CU(cudaMemcpyAsync(out, slots, n * samples * sizeof(unsigned long long), cudaMemcpyDeviceToHost, g_stream));
+    return sync_stream();
+}
+}  // namespace
+
 int gol_population_trace(gol_handle h, int64_t every, size_t n, uint64_t *out) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!valid(h) || (!out && n)) return fail(GOL_EINVAL, "invalid handle or null output");
-    if (every < 1) return fail(GOL_EINVAL, "every must be >= 1");
-    if (n == 0) return GOL_OK;
-    Scratch st(n * sizeof(unsigned long long));
-    if (!st.p) return fail(GOL_ENOMEM, "population trace scratch");
-    unsigned long long *slots = (unsigned long long *)st.p;
-    CU(cudaMemsetAsync(slots, 0, n * sizeof(unsigned long long), g_stream));
-    for (size_t i = 0; i < n; ++i) {
-        int rc = step_batch_locked(&h, &every, 1);
-        if (rc) return rc;
-        if (h->layout == GOL_LAYOUT_PACKED)
-            CU(launch_popcount_packed((const uint64_t *)h->buf[h->cur], h->srows * h->swords, slots + i, g_stream));
-        else
-            CU(launch_popcount_bytes((const uint8_t *)h->buf[h->cur], h->rows * h->cols, slots + i, g_stream));
-    }
-    CU(cudaMemcpyAsync(out, slots, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, g_stream));
-    return sync_stream();
+    if (!valid(h)) return fail(GOL_EINVAL, "invalid handle");
+    return population_trace_locked(&h, 1, every, n, out);
+}
+
+int gol_population_trace_batch(const gol_handle *hs, size_t n, int64_t every, size_t samples, uint64_t *out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return population_trace_locked(hs, n, every, samples, out);
 }
 
 namespace {
@@ -1301,13 +1432,16 @@ int step_batch_locked(const gol_handle *hs, const int64_t *generations, size_t n
             int rc = step_bytes(hs[i], generations[i]);
             if (rc) return rc;
         }
-    // packed boards: torus and bounded groups, split into launches of at most
+    // packed boards: torus and bounded groups, boards with and without a
+    // masked last word apart, split into launches of at most
     // kMaxGensPerLaunch generations
-    for (int torus = 1; torus >= 0; --torus) {
+    for (int group = 0; group < 4; ++group) {
+        const int torus = group < 2 ? 1 : 0, masked = group & 1;
         std::vector<gol_handle> grp;
         std::vector<int64_t> left;
         for (size_t i = 0; i < n; ++i)
-            if (hs[i]->layout == GOL_LAYOUT_PACKED && hs[i]->torus == torus && generations[i] > 0) {
+            if (hs[i]->layout == GOL_LAYOUT_PACKED && hs[i]->torus == torus && hs[i]->masked == masked &&
+                generations[i] > 0) {
                 grp.push_back(hs[i]);
                 left.push_back(generations[i]);
             }
@@ -1455,6 +1589,23 @@ int gol_tune_get(int64_t rows, int64_t cols, int *k, int *tile_rows) {
     TuneEntry t = tune_lookup(rows, cols);
     if (k) *k = supported_k(t.k);
     if (tile_rows) *tile_rows = t.rows;
+    return GOL_OK;
+}
+
+int gol_tune_class(int64_t rows, int64_t cols, int *row_class, int *word_class) {
+    if (rows < 1 || cols < 1) return fail(GOL_EINVAL, "bad size");
+    const std::pair<int, int> c = size_class(rows, cols);
+    if (row_class) *row_class = c.first;
+    if (word_class) *word_class = c.second;
+    return GOL_OK;
+}
+
+int gol_board_storage(gol_handle h, int64_t *srows, int64_t *swords, int *transposed) {
+    if (!valid(h)) return fail(GOL_EINVAL, "invalid handle");
+    const bool packed = h->layout == GOL_LAYOUT_PACKED;
+    if (srows) *srows = packed ? h->srows : h->rows;
+    if (swords) *swords = packed ? h->swords : 0;
+    if (transposed) *transposed = packed ? h->transposed : 0;
     return GOL_OK;
 }
 

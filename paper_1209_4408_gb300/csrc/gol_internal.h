@@ -42,7 +42,9 @@ struct BoardDesc {
     int32_t npass;    // passes in this launch (>= 1)
     int32_t gens;     // generations in this launch (>= npass)
     int32_t nunits;   // units of this board
-    int32_t pad;
+    int32_t ppp;      // population trace: passes per sampling period (0 = no trace); see pass_gens
+    int32_t pop_off;  // population trace: the board's first sample slot in PersistArgs::pop
+    int32_t last_bits;// masked last word: valid columns of each row's last word (1..63), 0 = all 64
 };
 
 // One unit (device memory).
@@ -76,7 +78,8 @@ struct __align__(128) UnitRun {
     int32_t r0, r_end, H, S, w0, U, mode, nnb;
     int32_t nb[kMaxNeighbours];
     int32_t cost;      // UnitDesc::cost
-    int32_t pad[2];
+    int32_t ppp;       // BoardDesc::ppp
+    int32_t pop_off;   // BoardDesc::pop_off
 };
 static_assert(sizeof(UnitRun) == 128, "UnitRun is one 128-byte line");
 
@@ -104,6 +107,7 @@ struct PersistArgs {
     int32_t nwarps;     // warps of the launch; warp w < hi_init starts with critical slot w
     int32_t pad;
     const int32_t *init_order;   // [nunits] units by ring: critical first passes, then the others
+    unsigned long long *pop;     // population trace: live cells per (board, sample) slot, or null
 };
 
 // One board of a many-board transfer: `nwords` words of the board buffer
@@ -143,7 +147,7 @@ struct CopyDesc {
     int64_t rows;       // board geometry in the interchange layout
     int64_t words;
     int32_t transposed; // board stored transposed (see gol_api.cu)
-    int32_t pad;
+    int32_t last_bits;  // masked last word: valid columns of the last word of a row, 0 = all 64
     int64_t block0;     // first block of this board in the copy grid
 };
 
@@ -194,7 +198,11 @@ cudaError_t launch_unpack_transposed(const uint64_t *store, int64_t R, int64_t C
 // `transposed`); to_res selects the direction.  src and dst must differ when
 // transposed.
 cudaError_t launch_orient(const uint64_t *src, uint64_t *dst, int64_t R, int64_t W, bool transposed, bool to_res,
-                          cudaStream_t s);
+                          cudaStream_t s, int last_bits = 0);
+// rows of any width C (W = ceil(C / 64) words per row, padding bits zero) to / from one byte per cell
+cudaError_t launch_pack_rows(const uint8_t *cells, uint64_t *words, int64_t R, int64_t C, int32_t *bad,
+                             cudaStream_t s);
+cudaError_t launch_unpack_rows(const uint64_t *words, uint8_t *cells, int64_t R, int64_t C, cudaStream_t s);
 cudaError_t launch_region_bytes(const uint8_t *cells, int64_t R, int64_t C, int64_t r0, int64_t c0,
                                 int64_t nr, int64_t nc, uint8_t *out, cudaStream_t s);
 cudaError_t launch_popcount_packed(const uint64_t *words, int64_t n, unsigned long long *out,

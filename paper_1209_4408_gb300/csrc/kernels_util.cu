@@ -44,11 +44,12 @@ __global__ void sched_init_kernel(PersistArgs a, int nboards) {
             r.S = u.S;
             r.w0 = u.w0;
             r.U = u.U;
-            r.mode = u.mode;
+            r.mode = u.mode | (b.last_bits << 8);   // the kernel reads the masked width from bits 8..15
             r.nnb = u.nnb;
             for (int k = 0; k < kMaxNeighbours; ++k) r.nb[k] = u.nb[k];
             r.cost = u.cost;
-            r.pad[0] = r.pad[1] = 0;
+            r.ppp = b.ppp;
+            r.pop_off = b.pop_off;
             a.run[i] = r;
             a.next_pass[i] = 1;            // every unit's first pass is queued below
             a.join[2 * i] = u.nnb + 1;     // join counters of both pass parities count down
@@ -183,7 +184,7 @@ __device__ __forceinline__ int64_t wrap(int64_t x, int64_t m) {
 __global__ void region_packed_kernel(const uint64_t *__restrict__ words, int64_t R, int64_t C,
                                      int64_t r0, int64_t c0, int64_t nr, int64_t nc,
                                      uint8_t *__restrict__ out, bool transposed) {
-    const int64_t n = nr * nc, W = C / 64;
+    const int64_t n = nr * nc, W = (C + 63) / 64;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t y = i / nc, x = i - y * nc;
@@ -448,12 +449,52 @@ __global__ void orient_super_kernel(const uint64_t *__restrict__ src, uint64_t *
 
 // R x W interchange words <-> resident storage in the same orientation
 // (transposed boards go through orient_super_kernel).
+// last_bits (1..63): the last word of every row holds that many columns and
+// its other bits are cleared on the way (0: whole words).
 __global__ void orient_kernel(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, int64_t R, int64_t W,
-                              bool to_res) {
+                              bool to_res, int last_bits) {
     const int64_t n = R * W;
+    const uint64_t keep = last_bits ? (1ull << last_bits) - 1 : ~0ull;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t w = src[i];
-        dst[i] = to_res ? to_resident(w) : to_interchange(w);
+        uint64_t w = src[i];
+        const bool last = i % W == W - 1;
+        if (to_res) {
+            if (last) w &= keep;
+            dst[i] = to_resident(w);
+        } else {
+            w = to_interchange(w);
+            dst[i] = last ? (w & keep) : w;
+        }
+    }
+}
+
+// Rows of C cells -> rows of ceil(C / 64) words (interchange layout, padding
+// zero); flags cell values other than 0 / 1.  One thread per word.
+__global__ void pack_rows_kernel(const uint8_t *__restrict__ cells, uint64_t *__restrict__ words, int64_t R,
+                                 int64_t C, int32_t *bad) {
+    const int64_t W = (C + 63) / 64, n = R * W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / W, k = i - r * W;
+        const uint8_t *p = cells + r * C + 64 * k;
+        const int m = (int)min((int64_t)64, C - 64 * k);
+        uint64_t w = 0;
+        bool high = false;
+        for (int j = 0; j < m; ++j) {
+            const uint8_t v = p[j];
+            high |= v > 1;
+            w |= (uint64_t)(v & 1) << j;
+        }
+        if (high) atomicExch(bad, 1);
+        words[i] = w;
+    }
+}
+
+__global__ void unpack_rows_kernel(const uint64_t *__restrict__ words, uint8_t *__restrict__ cells, int64_t R,
+                                   int64_t C) {
+    const int64_t n = R * C, W = (C + 63) / 64;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / C, c = i - r * C;
+        cells[i] = (uint8_t)((words[r * W + (c >> 6)] >> (c & 63)) & 1u);
     }
 }
 
@@ -467,8 +508,12 @@ __global__ void scatter_boards_kernel(const CopyDesc *__restrict__ d, const int3
     const int64_t lb = blockIdx.x - c.block0;
     if (!c.transposed) {
         const int64_t end = min(c.nwords, (lb + 1) * kCopyWordsPerBlock);
-        for (int64_t i = lb * kCopyWordsPerBlock + threadIdx.x; i < end; i += blockDim.x)
-            c.buf[0][i] = to_resident(staging[c.offset + i]);
+        const uint64_t keep = c.last_bits ? (1ull << c.last_bits) - 1 : ~0ull;
+        for (int64_t i = lb * kCopyWordsPerBlock + threadIdx.x; i < end; i += blockDim.x) {
+            uint64_t w = staging[c.offset + i];
+            if (i % c.words == c.words - 1) w &= keep;
+            c.buf[0][i] = to_resident(w);
+        }
     } else {
         // super-tile lb of the board (rows x words interchange) -> its stored transpose
         const int64_t nsj = (c.words + kSuper - 1) / kSuper;
@@ -588,15 +633,29 @@ cudaError_t launch_unpack_transposed(const uint64_t *store, int64_t R, int64_t C
     return cudaGetLastError();
 }
 
+cudaError_t launch_pack_rows(const uint8_t *cells, uint64_t *words, int64_t R, int64_t C, int32_t *bad,
+                             cudaStream_t s) {
+    const int64_t n = R * ((C + 63) / 64);
+    if (n > 0) pack_rows_kernel<<<grid_for(n), kBlock, 0, s>>>(cells, words, R, C, bad);
+    if (n > 0) count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_rows(const uint64_t *words, uint8_t *cells, int64_t R, int64_t C, cudaStream_t s) {
+    if (R * C > 0) unpack_rows_kernel<<<grid_for(R * C), kBlock, 0, s>>>(words, cells, R, C);
+    if (R * C > 0) count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_orient(const uint64_t *src, uint64_t *dst, int64_t R, int64_t W, bool transposed, bool to_res,
-                          cudaStream_t s) {
+                          cudaStream_t s, int last_bits) {
     if (R * W == 0) return cudaSuccess;
     if (transposed) {
         const int64_t nsuper = ((R / 64 + kSuper - 1) / kSuper) * ((W + kSuper - 1) / kSuper);
         orient_super_kernel<<<(unsigned)nsuper, kBlock, 0, s>>>(src, dst, R, W, to_res);
         count_launches(1);
     } else {
-        orient_kernel<<<grid_for(R * W, kBlock, 1 << 16), kBlock, 0, s>>>(src, dst, R, W, to_res);
+        orient_kernel<<<grid_for(R * W, kBlock, 1 << 16), kBlock, 0, s>>>(src, dst, R, W, to_res, last_bits);
         count_launches(1);
     }
     return cudaGetLastError();

@@ -125,7 +125,7 @@ __device__ __forceinline__ void run_unit_pass_moves(const UnitRun &ud,
     int seg = 0, word = 0, west_src = lane, east_src = lane;
     bool loads = false, stores = false;
     uint32_t west_mask = ~0u, east_mask = ~0u, lane_mask = ~0u;
-    if (ud.mode == kUnitFull) {
+    if ((ud.mode & 0xff) == kUnitFull) {
         seg = lane / W;
         word = lane - seg * W;
         if (seg < ud.S) {
@@ -277,7 +277,17 @@ __device__ __forceinline__ void run_unit_pass_moves(const UnitRun &ud,
 
 
 // Variant whose window slots rotate by renaming (loop unrolled three times).
-template <int K, bool TORUS, bool PARTIAL>
+//
+// MASKED: a board whose width C is not a multiple of 64, stored with
+// ceil(C / 64) words per row, the last word holding C' = C mod 64 columns
+// (ud.mode >> 8) and zero padding above them.  In every stage the lane that
+// holds the last word (a) writes column 0's state (the east word's bit 0,
+// zero on a bounded board) into the first padding column, which is then the
+// east neighbour of column C - 1, and (b) sends word 0's lane a value whose
+// bit 31 is column C - 1, its west neighbour across the wrap.  No real cell
+// has any other padding cell as a neighbour, so the padding needs no other
+// care inside a pass; stored rows have their padding cleared.
+template <int K, bool TORUS, bool PARTIAL, bool MASKED = false>
 __device__ __forceinline__ void run_unit_pass(const UnitRun &ud,
                                               const uint64_t *__restrict__ src,
                                               uint64_t *__restrict__ dst, int kk) {
@@ -291,7 +301,7 @@ __device__ __forceinline__ void run_unit_pass(const UnitRun &ud,
     int seg = 0, word = 0, west_src = lane, east_src = lane;
     bool loads = false, stores = false;
     uint32_t west_mask = ~0u, east_mask = ~0u, lane_mask = ~0u;
-    if (ud.mode == kUnitFull) {
+    if ((ud.mode & 0xff) == kUnitFull) {
         seg = lane / W;
         word = lane - seg * W;
         if (seg < ud.S) {
@@ -325,6 +335,29 @@ __device__ __forceinline__ void run_unit_pass(const UnitRun &ud,
     const int a = ud.r0 + seg * ud.H;                       // first output row of the segment
     const int seg_end = min(a + ud.H, ud.r_end);            // one past its last output row
     const int nmain = ud.H;                                 // main-loop iterations
+
+    // ---- masked last word (see above) --------------------------------
+    // last lane: pad_shift / pad_l / pad_h place column 0's bit at the first
+    // padding column (even C': low half bit C'/2, odd C': high half bit
+    // (C'-1)/2); west_n / west_pick make bit 31 of the value sent west
+    // column C - 1 (even C': high half bit C'/2 - 1, odd C': low half bit
+    // (C'-1)/2); keep_l / keep_h clear the padding of stored words.  Other
+    // lanes: all masks zero, west_n = 0 (they send their high half).
+    uint32_t pad_shift = 0, pad_l = 0, pad_h = 0, west_n = 0, west_pick = 0, keep_l = ~0u, keep_h = ~0u;
+    if (MASKED) {
+        const int cl = (ud.mode >> 8) & 0xff;               // valid columns of the last word, 1 .. 63
+        if (loads && word == W - 1) {
+            pad_shift = (uint32_t)(cl >> 1);
+            if (cl & 1)
+                pad_h = 1u << pad_shift;
+            else
+                pad_l = 1u << pad_shift;
+            west_n = (uint32_t)((cl + 1) >> 1);
+            west_pick = (cl & 1) ? ~0u : 0u;
+            keep_l = ((cl + 1) >> 1) >= 32 ? ~0u : (1u << ((cl + 1) >> 1)) - 1u;
+            keep_h = (1u << (cl >> 1)) - 1u;
+        }
+    }
 
     // ---- input row stream: row (a - K + j) of src ---------------------
     int lrow = a - K;                                       // row of the next load (unwrapped)
@@ -378,8 +411,15 @@ __device__ __forceinline__ void run_unit_pass(const UnitRun &ud,
 #pragma unroll
         for (int g = 0; g < K; ++g) {
             if (GUARD && j < 2 * g) break;                  // input of stage g not produced yet
-            const uint32_t wh = __shfl_sync(kFull, xh, west_src) & west_mask;
+            uint32_t wsend = xh;
+            if (MASKED) wsend = __funnelshift_rc(xh, lop3<0xD8>(xh, xl, west_pick), west_n);   // shift 32: the high word
+            const uint32_t wh = __shfl_sync(kFull, wsend, west_src) & west_mask;
             const uint32_t el = __shfl_sync(kFull, xl, east_src) & east_mask;
+            if (MASKED) {
+                const uint32_t t = el << pad_shift;
+                xl = lop3<0xD8>(xl, t, pad_l);              // pad_l ? t : xl, bit by bit
+                xh = lop3<0xD8>(xh, t, pad_h);
+            }
             // even columns (low half): west = odd column to the left = the
             // high half shifted up by one, its bit 0 from the west word;
             // east = the odd column to the right = the high half as is.
@@ -419,6 +459,10 @@ __device__ __forceinline__ void run_unit_pass(const UnitRun &ud,
     int orow = a;                                           // row of the next output
     uint64_t *outp = dst + word;
     auto emit = [&](uint2 o) {
+        if (MASKED) {
+            o.x &= keep_l;
+            o.y &= keep_h;
+        }
         if (stores && orow < seg_end) st_u64(outp + (size_t)orow * W, o.x, o.y);
         ++orow;
     };
@@ -481,7 +525,7 @@ __device__ __forceinline__ void run_unit_pass_skew(const UnitRun &ud,
     int seg = 0, word = 0, west_src = lane, east_src = lane;
     bool loads = false, stores = false;
     uint32_t west_mask = ~0u, east_mask = ~0u, lane_mask = ~0u;
-    if (ud.mode == kUnitFull) {
+    if ((ud.mode & 0xff) == kUnitFull) {
         seg = lane / W;
         word = lane - seg * W;
         if (seg < ud.S) {
@@ -648,9 +692,52 @@ __device__ __forceinline__ void run_unit_pass_skew(const UnitRun &ud,
 // ---------------------------------------------------------------------------
 // Scheduler
 // ---------------------------------------------------------------------------
+// Generations of pass `pass` (1-based) of a unit.  Without a population
+// trace the board's generations are spread over its passes, the first
+// ones one longer.  With a trace (ppp > 0) the launch is npass / ppp
+// sampling periods of P = gens / (npass / ppp) generations, each run in ppp
+// passes (the first ones one longer), so every sampled generation ends a
+// pass: the last pass of each period.
 __device__ __forceinline__ int pass_gens(const UnitRun &r, int pass) {
+    if (r.ppp > 0) {
+        const int P = r.gens / (r.npass / r.ppp), q = (pass - 1) % r.ppp;
+        const int base = P / r.ppp, rem = P - base * r.ppp;
+        return base + (q < rem ? 1 : 0);
+    }
     const int base = r.gens / r.npass, rem = r.gens - base * r.npass;
     return base + (pass <= rem ? 1 : 0);
+}
+
+// Whole warp, after a pass that ends a sampling period of a population
+// trace: the live cells of the words this warp stored in the pass (each
+// lane reads back its own stores), reduced over the warp.  The units of a
+// board cover its cells exactly once, so the board's count is the sum over
+// its units.
+__device__ __forceinline__ unsigned long long count_unit_output(const UnitRun &ud, const uint64_t *dst) {
+    const int lane = threadIdx.x & 31;
+    int seg = 0, word = 0;
+    bool stores = false;
+    if ((ud.mode & 0xff) == kUnitFull) {
+        seg = lane / ud.W;
+        word = lane - seg * ud.W;
+        stores = seg < ud.S;
+    } else {
+        stores = lane >= 1 && lane <= ud.U;
+        word = ud.w0 - 1 + lane;
+        if (word >= ud.W) word -= ud.W;                 // tiles may wrap on a torus
+    }
+    unsigned long long c = 0;
+    if (stores) {
+        const int a = ud.r0 + seg * ud.H, e = min(a + ud.H, ud.r_end);
+        const uint64_t *p = dst + word;
+        for (int row = a; row < e; ++row) {
+            const uint2 v = ld_cg_u64(p + (size_t)row * ud.W);
+            c += __popc(v.x) + __popc(v.y);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    return c;
 }
 
 __device__ __forceinline__ int ld_relaxed(const int32_t *p) {
@@ -829,6 +916,15 @@ __device__ __forceinline__ int complete_pass(const PersistArgs &A, int u, int pa
     return next;
 }
 
+// Kernel variants: 0 window shift by register moves, 1 window slots rotated
+// by renaming, 2 renaming with skewed stages, 3 = 1 held to three warps per
+// scheduler at K = 8; 4, 5, 6 = 1 for boards with a masked last word (4),
+// counting live cells for a population trace (5), or both (6), instantiated
+// for K = 4, 6 and 8 only (kMaskedPopK).
+constexpr bool variant_masked(int v) { return v == 4 || v == 6; }
+constexpr bool variant_pop(int v) { return v == 5 || v == 6; }
+constexpr bool variant_renaming(int v) { return v == 1 || v >= 3; }
+
 // Blocks per SM the register allocation must allow (GOL_MIN_BLOCKS for
 // K = 4..6 and GOL_MIN_BLOCKS_K8 for K = 8 at build time; 1 leaves the
 // choice to the compiler).
@@ -874,21 +970,26 @@ persistent_step_kernel(const PersistArgs A) {
         const uint64_t *src = r.buf[(r.cur + pass - 1) & 1];
         uint64_t *dst = r.buf[(r.cur + pass) & 1];
         const int kk = pass_gens(r, pass);
+        constexpr bool MASKED = variant_masked(VARIANT);
         if (VARIANT == 0) {
             if (kk == K)
                 run_unit_pass_moves<K, TORUS, false>(r, src, dst, K);
             else
                 run_unit_pass_moves<K, TORUS, true>(r, src, dst, kk);
-        } else if (VARIANT == 1 || VARIANT == 3) {
+        } else if (variant_renaming(VARIANT)) {
             if (kk == K)
-                run_unit_pass<K, TORUS, false>(r, src, dst, K);
+                run_unit_pass<K, TORUS, false, MASKED>(r, src, dst, K);
             else
-                run_unit_pass<K, TORUS, true>(r, src, dst, kk);
+                run_unit_pass<K, TORUS, true, MASKED>(r, src, dst, kk);
         } else {
             if (kk == K)
                 run_unit_pass_skew<K, TORUS, false>(r, src, dst, K);
             else
                 run_unit_pass_skew<K, TORUS, true>(r, src, dst, kk);
+        }
+        if (variant_pop(VARIANT) && r.ppp > 0 && pass % r.ppp == 0) {
+            const unsigned long long c = count_unit_output(r, dst);
+            if (lane == 0) atomicAdd(&A.pop[r.pop_off + pass / r.ppp - 1], c);
         }
         // every lane's stores of this pass (and the counter reset) are ordered
         // before the counter updates that publish it (acquire-release fence,
@@ -921,49 +1022,52 @@ persistent_step_kernel(const PersistArgs A) {
     }
 }
 
-template <int K>
-cudaError_t launch_persistent_impl(const PersistArgs &a, bool torus, int variant, int grid, cudaStream_t s) {
-    if (variant == 0) {
-        if (torus)
-            persistent_step_kernel<K, true, 0><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
-        else
-            persistent_step_kernel<K, false, 0><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
-    } else if (variant == 1 || (variant == 3 && K != 8)) {
-        if (torus)
-            persistent_step_kernel<K, true, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
-        else
-            persistent_step_kernel<K, false, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
-    } else if (variant == 3) {
-        if (torus)
-            persistent_step_kernel<K, true, (K == 8 ? 3 : 1)><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
-        else
-            persistent_step_kernel<K, false, (K == 8 ? 3 : 1)><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
-    } else {
-        if (torus)
-            persistent_step_kernel<K, true, 2><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
-        else
-            persistent_step_kernel<K, false, 2><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
-    }
+template <int K, int V>
+cudaError_t launch_variant(const PersistArgs &a, bool torus, int grid, cudaStream_t s) {
+    if (torus)
+        persistent_step_kernel<K, true, V><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
+    else
+        persistent_step_kernel<K, false, V><<<grid, kWarpsPerBlock * 32, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
+template <int K, int V>
+cudaError_t occupancy_variant(bool torus, int *bps) {
+    const int t = kWarpsPerBlock * 32;
+    return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, V>, t, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, V>, t, 0);
+}
+
+// generations per pass with instantiations of variants 4, 5 and 6
+constexpr bool masked_pop_k(int k) { return k == 4 || k == 6 || k == 8; }
+
+template <int K>
+cudaError_t launch_persistent_impl(const PersistArgs &a, bool torus, int variant, int grid, cudaStream_t s) {
+    if constexpr (masked_pop_k(K)) {
+        if (variant == 4) return launch_variant<K, 4>(a, torus, grid, s);
+        if (variant == 5) return launch_variant<K, 5>(a, torus, grid, s);
+        if (variant == 6) return launch_variant<K, 6>(a, torus, grid, s);
+    }
+    if (variant >= 4) return cudaErrorInvalidValue;
+    if (variant == 0) return launch_variant<K, 0>(a, torus, grid, s);
+    if (variant == 2) return launch_variant<K, 2>(a, torus, grid, s);
+    if (variant == 3 && K == 8) return launch_variant<K, (K == 8 ? 3 : 1)>(a, torus, grid, s);
+    return launch_variant<K, 1>(a, torus, grid, s);
+}
+
 template <int K>
 cudaError_t persistent_occupancy_impl(bool torus, int variant, int *bps) {
-    const int t = kWarpsPerBlock * 32;
-    if (variant == 0)
-        return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, 0>, t, 0)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, 0>, t, 0);
-    if (variant == 1 || (variant == 3 && K != 8))
-        return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, 1>, t, 0)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, 1>, t, 0);
-    if (variant == 3)
-        return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, (K == 8 ? 3 : 1)>,
-                                                                     t, 0)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, (K == 8 ? 3 : 1)>,
-                                                                     t, 0);
-    return torus ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, true, 2>, t, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, persistent_step_kernel<K, false, 2>, t, 0);
+    if constexpr (masked_pop_k(K)) {
+        if (variant == 4) return occupancy_variant<K, 4>(torus, bps);
+        if (variant == 5) return occupancy_variant<K, 5>(torus, bps);
+        if (variant == 6) return occupancy_variant<K, 6>(torus, bps);
+    }
+    if (variant >= 4) return cudaErrorInvalidValue;
+    if (variant == 0) return occupancy_variant<K, 0>(torus, bps);
+    if (variant == 2) return occupancy_variant<K, 2>(torus, bps);
+    if (variant == 3 && K == 8) return occupancy_variant<K, (K == 8 ? 3 : 1)>(torus, bps);
+    return occupancy_variant<K, 1>(torus, bps);
 }
 
 #define GOL_INSTANTIATE_PERSISTENT(KV)                                                             \

@@ -49,10 +49,12 @@ EXPORTED = (
     "gol_create", "gol_create_ex", "gol_destroy", "gol_set", "gol_get", "gol_set_packed",
     "gol_get_packed", "gol_set_packed_device", "gol_get_packed_device", "gol_set_packed_batch",
     "gol_get_packed_batch", "gol_get_region",
-    "gol_step", "gol_step_batch", "gol_population", "gol_population_trace", "gol_generation", "gol_info",
+    "gol_step", "gol_step_batch", "gol_population", "gol_population_trace", "gol_population_trace_batch",
+    "gol_generation", "gol_info",
     "gol_sync",
     "gol_set_stream", "gol_set_allocator", "gol_last_error", "gol_set_option", "gol_get_option",
-    "gol_tune_set", "gol_tune_get", "gol_tune_reset", "gol_device_info", "gol_probe_int_throughput",
+    "gol_tune_set", "gol_tune_get", "gol_tune_reset", "gol_tune_class", "gol_board_storage", "gol_device_info",
+    "gol_probe_int_throughput",
     "gol_debug_unfilled_wait", "gol_step_packed_noalloc", "gol_plan_units", "gol_kernel_launches",
 )
 
@@ -96,6 +98,7 @@ def load() -> ctypes.CDLL:
         "gol_step_batch": [vp, vp, sz],
         "gol_population": [vp, P(ctypes.c_uint64)],
         "gol_population_trace": [vp, i64, sz, vp],
+        "gol_population_trace_batch": [vp, sz, i64, sz, vp],
         "gol_generation": [vp, P(i64)],
         "gol_info": [vp, P(i64), P(i64), P(i32), P(i32)],
         "gol_sync": [vp],
@@ -107,6 +110,8 @@ def load() -> ctypes.CDLL:
         "gol_tune_set": [i64, i64, i32, i32],
         "gol_tune_get": [i64, i64, P(i32), P(i32)],
         "gol_tune_reset": [],
+        "gol_tune_class": [i64, i64, P(i32), P(i32)],
+        "gol_board_storage": [vp, P(i64), P(i64), P(i32)],
         "gol_device_info": [P(i32), P(i64), P(i32)],
         "gol_probe_int_throughput": [P(ctypes.c_double), P(ctypes.c_double)],
         "gol_debug_unfilled_wait": [i64],
@@ -181,7 +186,7 @@ def gol_set_packed(h: int, words: np.ndarray):
 def gol_get_packed(h: int, out: np.ndarray | None = None) -> np.ndarray:
     R, C, _, _ = gol_info(h)
     if out is None:
-        out = np.empty((R, C // 64), dtype=np.uint64)
+        out = np.empty((R, (C + 63) // 64), dtype=np.uint64)
     _check(load().gol_get_packed(h, _ptr(out), out.size))
     return out
 
@@ -251,6 +256,15 @@ def gol_population(h: int) -> int:
 def gol_population_trace(h: int, every: int, n: int) -> np.ndarray:
     out = np.zeros(n, dtype=np.uint64)
     _check(load().gol_population_trace(h, int(every), int(n), _ptr(out) if n else None))
+    return out
+
+
+def gol_population_trace_batch(hs: Sequence[int], every: int, samples: int) -> np.ndarray:
+    """uint64[len(hs), samples]: live cells of each board after every ``every`` generations."""
+    h = _handles(hs)
+    out = np.zeros((h.size, samples), dtype=np.uint64)
+    _check(load().gol_population_trace_batch(_ptr(h), h.size, int(every), int(samples),
+                                             _ptr(out) if out.size else None))
     return out
 
 
@@ -345,6 +359,19 @@ def gol_tune_get(rows: int, cols: int):
 
 def gol_tune_reset():
     _check(load().gol_tune_reset())
+
+
+def gol_tune_class(rows: int, cols: int):
+    r, w = ctypes.c_int(), ctypes.c_int()
+    _check(load().gol_tune_class(rows, cols, ctypes.byref(r), ctypes.byref(w)))
+    return r.value, w.value
+
+
+def gol_board_storage(h: int):
+    """(stored rows, stored words per row, transposed) of a board."""
+    r, w, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    _check(load().gol_board_storage(h, ctypes.byref(r), ctypes.byref(w), ctypes.byref(t)))
+    return r.value, w.value, bool(t.value)
 
 
 UNIT_FIELDS = 17

@@ -114,6 +114,17 @@ def random_words_region(words_per_row: int, seed: int, r0: int, nr: int,
     return sm64(idx + np.uint64(seed & _MASK64))
 
 
+def pack_rows(cells: np.ndarray) -> np.ndarray:
+    """uint8[R, C] (any C) -> uint64[R, ceil(C/64)] in the packed convention,
+    the bits past column C of each row's last word zero."""
+    cells = np.ascontiguousarray(cells, dtype=np.uint8)
+    R, C = cells.shape
+    W = (C + 63) // 64
+    padded = np.zeros((R, 64 * W), dtype=np.uint8)
+    padded[:, :C] = cells
+    return pack_cells(padded)
+
+
 def pack_cells(cells: np.ndarray) -> np.ndarray:
     """uint8[R, C] (C % 64 == 0) -> uint64[R, C/64] in the packed convention."""
     cells = np.ascontiguousarray(cells, dtype=np.uint8)
@@ -163,6 +174,7 @@ SEED_SINGLE_16K = 14410     # 16384^2 packed board, Bernoulli(0.5)
 SEED_BATCH_4096 = 14411     # 4096-board batch
 SEED_SERVE = 14412          # request stream
 SEED_HUGE_128K = 14413      # 131072^2 board with a glider band
+SEED_MASKED = 14414         # board with neither side a multiple of 64
 
 
 def _round64(x: float, lo: int, hi: int) -> int:

@@ -51,3 +51,39 @@ def test_tune_shape_on_gpu(mods):
     assert np.array_equal(b.get(), oracle.run(cells, 33))
     b.close()
     gol.gol_tune_reset()
+
+
+@pytest.mark.gpu
+def test_tune_batch_on_gpu(mods):
+    # per-class tuning on a small batch: the classes are ranked by work, the
+    # entries found are installed, and the batch stays exact under them
+    autotune, gol = mods
+    import torch
+
+    gol.gol_set_stream(torch.cuda.current_stream())
+    specs = synth.batch_specs(40, seed=77, side_hi=512, gen_hi=200)
+    boards, cells = [], []
+    for s in specs:
+        c = synth.bernoulli_board(s.rows, s.cols, s.density, s.seed)
+        b = gol.Board(s.rows, s.cols)
+        b.set(c)
+        boards.append(b)
+        cells.append(c)
+    hs = [b.handle for b in boards]
+    gens = [s.gens for s in specs]
+    cls = autotune.batch_classes(hs, gens)
+    assert abs(sum(c["share"] for c in cls) - 1.0) < 1e-9
+    assert [c["work"] for c in cls] == sorted((c["work"] for c in cls), reverse=True)
+    res = autotune.tune_batch(hs, gens, classes=2, tile_rows=(16, 64), ks=(4, 6), steps=1, warmup=1)
+    assert len(res["entries"]) == 2 and res["after_s"] > 0
+    for e in res["entries"]:
+        assert gol.gol_tune_get(e["rows"], e["cols"]) == (e["k"], e["tile_rows"])
+    for b, c in zip(boards, cells):           # restart from the initial cells under the tuned table
+        b.set(c)
+    gol.gol_step_batch(hs, gens)
+    for b, c, s in zip(boards, cells, specs):
+        assert np.array_equal(b.get(), oracle.run(c, s.gens)), (s.rows, s.cols, s.gens)
+        b.close()
+    gol.gol_tune_reset()
+    autotune.load_shipped()
+    gol.gol_set_stream(None)

@@ -380,10 +380,12 @@ def test_torch_allocator_and_stream(gol):
 
 
 def test_invalid_arguments(gol):
-    # packed needs a width or a height that is a multiple of 64
+    # packed boards of any size (a partial last word when neither side is a
+    # multiple of 64); an unknown layout is rejected
     with pytest.raises(gol.GolError) as e:
-        gol.gol_create_ex(30, 100, True, gol.GOL_LAYOUT_PACKED)
+        gol.gol_create_ex(30, 100, True, 7)
     assert e.value.code == gol.GOL_EINVAL
+    gol.gol_destroy(gol.gol_create_ex(30, 100, True, gol.GOL_LAYOUT_PACKED))
     gol.gol_destroy(gol.gol_create_ex(64, 100, True, gol.GOL_LAYOUT_PACKED))
     b = gol.Board(8, 64)
     bad = np.zeros((8, 64), np.uint8)
@@ -582,3 +584,49 @@ def test_bytes_graph_replay_on_torch_stream(gol):
     finally:
         gol.gol_set_option(gol.GOL_OPT_BYTE_CLUSTER, 1)
         gol.gol_set_stream(None)
+
+
+@pytest.mark.parametrize("every", [1, 4, 7, 13])
+def test_population_trace_batch(gol, every):
+    # several boards traced at once: packed boards are counted inside the
+    # step kernel at the end of the passes that end a sampling period (6
+    # generations per pass: a period of 7 runs as passes of 4 + 3, 13 as
+    # 5 + 4 + 4), byte boards sample by sample; torus and bounded, one unit
+    # and many, full rows and word tiles, boards stored transposed
+    shapes = [(96, 192, True), (640, 2176, True), (64, 3 * 64, True), (128, 100, True), (200, 64 * 40, False),
+              (130, 256, False), (33, 47, True)]
+    gol.gol_set_option(gol.GOL_OPT_GENS_PER_PASS, 6)
+    gol.gol_set_option(gol.GOL_OPT_TILE_ROWS, 32)
+    try:
+        boards, cells = [], []
+        for i, (R, C, torus) in enumerate(shapes):
+            c = synth.bernoulli_board(R, C, 0.35, 500 + i)
+            b = gol.Board(R, C, torus=torus)
+            b.set(c)
+            boards.append(b)
+            cells.append(c)
+        samples = 9
+        got = gol.gol_population_trace_batch([b.handle for b in boards], every, samples)
+        assert got.shape == (len(shapes), samples)
+        for i, ((R, C, torus), c, b) in enumerate(zip(shapes, cells, boards)):
+            x, want = c, []
+            for _ in range(samples):
+                x = oracle.run(x, every, torus)
+                want.append(oracle.population(x))
+            assert [int(v) for v in got[i]] == want, "board %d (%d x %d, torus %s)" % (i, R, C, torus)
+            assert b.generation() == samples * every
+            assert_same(b.get(), x, "board %d after the trace" % i)
+        for b in boards:
+            b.close()
+    finally:
+        gol.gol_set_option(gol.GOL_OPT_GENS_PER_PASS, 0)
+        gol.gol_set_option(gol.GOL_OPT_TILE_ROWS, 0)
+
+
+def test_population_trace_batch_rejects_bad_arguments(gol):
+    b = gol.Board(64, 64)
+    with pytest.raises(gol.GolError):
+        gol.gol_population_trace_batch([b.handle, b.handle], 3, 2)
+    with pytest.raises(gol.GolError):
+        gol.gol_population_trace_batch([b.handle], 0, 2)
+    b.close()

@@ -171,10 +171,13 @@ def lop3_words(lut, a, b, c):
 
 def funnelshift(kind, lo, hi, n):
     """CUDA __funnelshift_l / __funnelshift_r: the high (l) or low (r) 32 bits
-    of the 64-bit value hi:lo shifted left / right by n & 31."""
+    of the 64-bit value hi:lo shifted left / right by n & 31; "rc" is
+    __funnelshift_rc, the right shift by min(n, 32)."""
     import numpy as np
 
     v = (hi.astype(np.uint64) << np.uint64(32)) | lo.astype(np.uint64)
+    if kind == "rc":
+        return (v >> np.uint64(min(n, 32))).astype(np.uint32)
     n = np.uint64(n & 31)
     if kind == "l":
         return ((v << n) >> np.uint64(32)).astype(np.uint32)
@@ -205,6 +208,8 @@ def row_sum_program(body):
     planes = []
     for m in re.finditer(r"(\w+)(?:\[\w+\])*\s*=\s*lop3<(\w+)>\((\w+),\s*(\w+),\s*(\w+)\)", body):
         name, lut, a, b, c = m.groups()
+        if name in ("xl", "xh"):
+            continue                    # the masked last word's padding patch (see masked_program)
         pm = re.fullmatch(r"[a-z]([01])([lh])", name)
         assert pm, name
         planes.append((int(pm.group(1)), pm.group(2), consts.get(lut, None) or int(lut, 0), a, b, c))
@@ -319,3 +324,78 @@ def test_one_generation_from_the_kernel_source_matches_the_oracle():
                             (below[(0, "h")], below[(1, "h")]), halves[r][1])
             nxt[r] = from_halves(lo, hi)
         assert np.array_equal(nxt, oracle.run(cells, 1)), (R, W)
+
+
+# ---------------------------------------------------------------------------
+# Boards whose width is not a multiple of 64: the masked stage arithmetic of
+# the renaming pass variant (the padding patch of the last word and the value
+# sent west to word 0), read from the source and run on rows of every width.
+# ---------------------------------------------------------------------------
+def masked_program(body):
+    """(wsend LUT, patch LUTs) of the MASKED lines of an iterate body."""
+    consts = lut_constants(source("wavefront.cuh"))
+    m = re.search(r"wsend = __funnelshift_rc\(xh, lop3<(\w+)>\(xh, xl, west_pick\), west_n\);", body)
+    assert m, "west value of the masked last word"
+    wlut = consts.get(m.group(1), None) or int(m.group(1), 0)
+    m = re.search(r"const uint32_t t = el << pad_shift;", body)
+    assert m, "padding bit shift"
+    pl = re.search(r"xl = lop3<(\w+)>\(xl, t, pad_l\);", body)
+    ph = re.search(r"xh = lop3<(\w+)>\(xh, t, pad_h\);", body)
+    assert pl and ph, "padding patches"
+    return wlut, int(pl.group(1), 0), int(ph.group(1), 0)
+
+
+def last_lane_constants(cl):
+    """The masked last word's lane constants as the kernel documents them:
+    column 0 goes to the first padding column (even C': low half bit C'/2,
+    odd C': high half bit (C'-1)/2); bit 31 of the value sent west is column
+    C - 1 (even C': high half bit C'/2 - 1, odd C': low half bit (C'-1)/2)."""
+    shift = cl >> 1
+    pad_l = 0 if cl & 1 else 1 << shift
+    pad_h = 1 << shift if cl & 1 else 0
+    return shift, pad_l, pad_h, (cl + 1) >> 1, (M32 if cl & 1 else 0)
+
+
+def test_masked_last_word_row_sums_every_width():
+    import numpy as np
+
+    bodies = iterate_bodies()
+    body = bodies[1]                                 # the renaming variant carries the masked path
+    wlut, plut, hlut = masked_program(body)
+    shifts, planes = row_sum_program(body)
+    rng = np.random.default_rng(46)
+    for C in list(range(1, 130)) + [191, 200]:
+        if C % 64 == 0:
+            continue
+        W, cl = (C + 63) // 64, C % 64
+        for trial in range(3):
+            row = (rng.random(C) < 0.5).astype(np.uint8)
+            padded = np.zeros(64 * W, np.uint8)
+            padded[:C] = row
+            lo, hi = to_halves(padded)
+            # padding of words that have left a stage is arbitrary: garbage
+            garbage = rng.integers(0, 1 << 32, size=2, dtype=np.uint64).astype(np.uint32)
+            keep_l = M32 if (cl + 1) >> 1 >= 32 else (1 << ((cl + 1) >> 1)) - 1
+            keep_h = (1 << (cl >> 1)) - 1
+            lo[-1] = (lo[-1] & np.uint32(keep_l)) | (garbage[0] & np.uint32(~keep_l & M32))
+            hi[-1] = (hi[-1] & np.uint32(keep_h)) | (garbage[1] & np.uint32(~keep_h & M32))
+            shift, pad_l, pad_h, west_n, pick = last_lane_constants(cl)
+            z = np.zeros(W, np.uint32)
+            sh, pl_, ph_, wn, pk = z.copy(), z.copy(), z.copy(), np.zeros(W, np.int64), z.copy()
+            sh[-1], pl_[-1], ph_[-1], wn[-1], pk[-1] = shift, pad_l, pad_h, west_n, pick
+            wsend = np.array([funnelshift("rc", hi[k:k + 1], lop3_words(wlut, hi[k:k + 1], lo[k:k + 1], pk[k:k + 1]),
+                                          int(wn[k]))[0] for k in range(W)], dtype=np.uint32)
+            wh, el = np.roll(wsend, 1), np.roll(lo, -1)
+            t = (el.astype(np.uint64) << sh.astype(np.uint64)).astype(np.uint64) & np.uint64(M32)
+            t = t.astype(np.uint32)
+            lo2, hi2 = lop3_words(plut, lo, t, pl_), lop3_words(hlut, hi, t, ph_)
+            env = {"xl": lo2, "xh": hi2, "wh": wh, "el": el}
+            for dst, (kind, a, b, n) in shifts.items():
+                env[dst] = funnelshift(kind, env[a], env[b], n)
+            got = {}
+            for plane, half, lut, a, b, c in planes:
+                got[(plane, half)] = lop3_words(lut, env[a], env[b], env[c])
+            hsum = np.roll(row, 1) + row + np.roll(row, -1)          # the C-column torus
+            for plane in (0, 1):
+                cells = from_halves(got[(plane, "l")], got[(plane, "h")])[:C]
+                assert np.array_equal(cells, (hsum >> plane) & 1), (C, plane)
