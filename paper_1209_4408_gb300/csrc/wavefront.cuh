@@ -344,8 +344,10 @@ __device__ __forceinline__ void run_unit_pass(const UnitRun &ud,
     // (C'-1)/2); keep_l / keep_h clear the padding of stored words.  Other
     // lanes: all masks zero, west_n = 0 (they send their high half).
     uint32_t pad_shift = 0, pad_l = 0, pad_h = 0, west_n = 0, west_pick = 0, keep_l = ~0u, keep_h = ~0u;
+    bool warp_last = false;                                 // some lane of this warp holds word W - 1
     if (MASKED) {
         const int cl = (ud.mode >> 8) & 0xff;               // valid columns of the last word, 1 .. 63
+        warp_last = __ballot_sync(kFull, loads && word == W - 1) != 0;
         if (loads && word == W - 1) {
             pad_shift = (uint32_t)(cl >> 1);
             if (cl & 1)
@@ -411,11 +413,14 @@ __device__ __forceinline__ void run_unit_pass(const UnitRun &ud,
 #pragma unroll
         for (int g = 0; g < K; ++g) {
             if (GUARD && j < 2 * g) break;                  // input of stage g not produced yet
+            // (warp_last is uniform over the warp: warps without the partial
+            // word, all tiles but one of a wide board, skip the masked steps)
             uint32_t wsend = xh;
-            if (MASKED) wsend = __funnelshift_rc(xh, lop3<0xD8>(xh, xl, west_pick), west_n);   // shift 32: the high word
+            if (MASKED && warp_last)
+                wsend = __funnelshift_rc(xh, lop3<0xD8>(xh, xl, west_pick), west_n);   // shift 32: the high word
             const uint32_t wh = __shfl_sync(kFull, wsend, west_src) & west_mask;
             const uint32_t el = __shfl_sync(kFull, xl, east_src) & east_mask;
-            if (MASKED) {
+            if (MASKED && warp_last) {
                 const uint32_t t = el << pad_shift;
                 xl = lop3<0xD8>(xl, t, pad_l);              // pad_l ? t : xl, bit by bit
                 xh = lop3<0xD8>(xh, t, pad_h);
