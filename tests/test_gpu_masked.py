@@ -159,3 +159,21 @@ def test_auto_layout_of_large_odd_boards_is_packed(gol):
     small = gol.Board(100, 130)                # fits a cluster: bytes
     assert small.layout == gol.GOL_LAYOUT_BYTES
     small.close()
+
+
+@pytest.mark.parametrize("k", [4, 6, 8])
+def test_masked_wide_boards_several_tiles(gol, k):
+    # 71 and 96 words per row (three and four word tiles; on the torus tile 0
+    # is rotated to hold the partial word and word 0), short row blocks
+    gol.gol_set_option(gol.GOL_OPT_GENS_PER_PASS, k)
+    gol.gol_set_option(gol.GOL_OPT_TILE_ROWS, 16)
+    try:
+        for (R, C, torus) in [(301, 64 * 70 + 13, True), (301, 64 * 70 + 13, False), (150, 64 * 95 + 50, True)]:
+            cells = synth.bernoulli_board(R, C, 0.45, R * 3 + C + k)
+            b = packed_board(gol, cells, torus)
+            b.step(2 * k + 3)
+            assert np.array_equal(b.get(), oracle.run_rows_omp(cells, 2 * k + 3, THREADS, torus)), (R, C, torus)
+            b.close()
+    finally:
+        gol.gol_set_option(gol.GOL_OPT_GENS_PER_PASS, 0)
+        gol.gol_set_option(gol.GOL_OPT_TILE_ROWS, 0)
