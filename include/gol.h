@@ -117,6 +117,16 @@ int gol_get_packed_device(gol_handle h, uint64_t *dwords, size_t nwords);
 int gol_set_packed_batch(const gol_handle *hs, size_t n, const uint64_t *words, size_t nwords);
 int gol_get_packed_batch(const gol_handle *hs, size_t n, uint64_t *words, size_t nwords);
 
+/* As gol_get_packed_batch without waiting: the copy is queued on the
+ * library's current stream and `words` holds the boards' states once that
+ * work has run (wait on the stream, or an event recorded on it after this
+ * call).  `words` must be page-locked memory for the call not to wait (a
+ * pageable buffer makes the final device-to-host copy synchronous), and the
+ * boards must not be stepped or destroyed on another stream meanwhile.
+ * With it a caller keeps several batches in flight on several streams:
+ * one batch's transfers overlap another's step. */
+int gol_get_packed_batch_async(const gol_handle *hs, size_t n, uint64_t *words, size_t nwords);
+
 /* Copies the nr x nc window whose top-left cell is (r0, c0) to host `out`
  * (nr*nc bytes, row major).  Window indices are taken modulo the board
  * size, so windows may straddle the wrap.  nr, nc >= 0. */

@@ -144,7 +144,12 @@ void dev_free(void *p, void (*ff)(void *, void *), void *ctx) {
         cudaFree(p);
 }
 
-// scoped temporary device buffer using the process allocator
+void defer_free(void *p, void (*ff)(void *, void *), void *ctx);
+
+// scoped temporary device buffer using the process allocator.  With an
+// allocator hook the buffer is returned once the work queued on the stream
+// so far has run (an event, see defer_free): the hook's allocator may hand
+// it out again to work on another stream.
 struct Scratch {
     void *p = nullptr;
     void *(*af)(size_t, void *) = g_alloc;
@@ -153,8 +158,12 @@ struct Scratch {
     explicit Scratch(size_t n) { p = dev_alloc(n, af, ctx); }
     ~Scratch() {
         if (p) {
-            if (!ff) cudaStreamSynchronize(g_stream);
-            dev_free(p, ff, ctx);
+            if (!ff) {
+                cudaStreamSynchronize(g_stream);
+                dev_free(p, ff, ctx);
+            } else {
+                defer_free(p, ff, ctx);
+            }
         }
     }
 };
@@ -675,6 +684,21 @@ void reap_boards(bool all) {
     }
 }
 
+// Frees p once the work queued so far on the library's stream has run.
+void defer_free(void *p, void (*ff)(void *, void *), void *ctx) {
+    if (!p) return;
+    BoardGrave g{{p, nullptr, nullptr}, ff, ctx, {nullptr, nullptr}, nullptr};
+    if (cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(g.ev, g_stream) != cudaSuccess) {
+        cudaGetLastError();
+        if (g.ev) cudaEventDestroy(g.ev);
+        cudaStreamSynchronize(g_stream);
+        free_board_memory(g);
+        return;
+    }
+    g_board_graves.push_back(g);
+}
+
 void clear_plans() {
     for (auto &p : g_plans) bury(std::move(p));
     g_plans.clear();
@@ -1141,8 +1165,12 @@ struct CopyPlan {
     const int32_t *block_board() const { return (const int32_t *)((const char *)dmem + board_off); }
     ~CopyPlan() {
         if (dmem) {
-            if (!free_fn) cudaStreamSynchronize(g_stream);
-            dev_free(dmem, free_fn, alloc_ctx);
+            if (!free_fn) {
+                cudaStreamSynchronize(g_stream);
+                dev_free(dmem, free_fn, alloc_ctx);
+            } else {
+                defer_free(dmem, free_fn, alloc_ctx);
+            }
         }
     }
 };
@@ -1277,6 +1305,26 @@ int gol_get_packed_batch(const gol_handle *hs, size_t n, uint64_t *words, size_t
     CU(launch_gather_boards(P->desc(), P->block_board(), P->blocks, dst ? dst : (uint64_t *)st->p, g_stream));
     if (!dst) CU(cudaMemcpyAsync(words, st->p, nwords * 8, cudaMemcpyDeviceToHost, g_stream));
     return sync_stream();
+}
+
+int gol_get_packed_batch_async(const gol_handle *hs, size_t n, uint64_t *words, size_t nwords) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (n == 0) return GOL_OK;
+    if (!words) return fail(GOL_EINVAL, "null words");
+    const CopyPlan *P = nullptr;
+    int rc = copy_plan(hs, n, &P);
+    if (rc) return rc;
+    if ((int64_t)nwords != P->nwords)
+        return fail(GOL_EINVAL, "nwords = %zu, the boards hold %lld words", nwords, (long long)P->nwords);
+    uint64_t *dst = (uint64_t *)mapped_host_pointer(words, *P);
+    std::unique_ptr<Scratch> st;
+    if (!dst) {
+        st.reset(new Scratch(nwords * 8));
+        if (!st->p) return fail(GOL_ENOMEM, "staging buffer of %zu bytes", nwords * 8);
+    }
+    CU(launch_gather_boards(P->desc(), P->block_board(), P->blocks, dst ? dst : (uint64_t *)st->p, g_stream));
+    if (!dst) CU(cudaMemcpyAsync(words, st->p, nwords * 8, cudaMemcpyDeviceToHost, g_stream));
+    return GOL_OK;
 }
 
 int gol_get_region(gol_handle h, int64_t r0, int64_t c0, int64_t nr, int64_t nc, uint8_t *out) {

@@ -48,7 +48,7 @@ GOL_OPT_CRITICAL_PERMILLE = 10
 EXPORTED = (
     "gol_create", "gol_create_ex", "gol_destroy", "gol_set", "gol_get", "gol_set_packed",
     "gol_get_packed", "gol_set_packed_device", "gol_get_packed_device", "gol_set_packed_batch",
-    "gol_get_packed_batch", "gol_get_region",
+    "gol_get_packed_batch", "gol_get_packed_batch_async", "gol_get_region",
     "gol_step", "gol_step_batch", "gol_population", "gol_population_trace", "gol_population_trace_batch",
     "gol_generation", "gol_info",
     "gol_sync",
@@ -93,6 +93,7 @@ def load() -> ctypes.CDLL:
         "gol_get_packed_device": [vp, vp, sz],
         "gol_set_packed_batch": [vp, sz, vp, sz],
         "gol_get_packed_batch": [vp, sz, vp, sz],
+        "gol_get_packed_batch_async": [vp, sz, vp, sz],
         "gol_get_region": [vp, i64, i64, i64, i64, vp],
         "gol_step": [vp, i64],
         "gol_step_batch": [vp, vp, sz],
@@ -217,6 +218,16 @@ def gol_get_packed_batch(hs: Sequence[int], out: np.ndarray) -> np.ndarray:
     if not (out.dtype == np.uint64 and out.flags.c_contiguous):
         raise ValueError("out must be a contiguous uint64 array")
     _check(load().gol_get_packed_batch(_ptr(h), h.size, _ptr(out), out.size))
+    return out
+
+
+def gol_get_packed_batch_async(hs: Sequence[int], out: np.ndarray) -> np.ndarray:
+    """Queues the download of the boards into ``out`` (page-locked for the
+    call not to wait); ``out`` is valid once the library's stream has run it."""
+    h = _handles(hs)
+    if not (out.dtype == np.uint64 and out.flags.c_contiguous):
+        raise ValueError("out must be a contiguous uint64 array")
+    _check(load().gol_get_packed_batch_async(_ptr(h), h.size, _ptr(out), out.size))
     return out
 
 

@@ -630,3 +630,49 @@ def test_population_trace_batch_rejects_bad_arguments(gol):
     with pytest.raises(gol.GolError):
         gol.gol_population_trace_batch([b.handle], 0, 2)
     b.close()
+
+
+def test_two_batches_in_flight_on_two_streams(gol):
+    # two sets of boards, each on its own stream, with uploads from pinned
+    # memory and asynchronous downloads: each set's results equal the oracle,
+    # whatever the other set's work in flight (staging buffers are returned
+    # only after the work that used them)
+    import torch
+
+    gol.use_torch_allocator()              # staging buffers from PyTorch's caching allocator
+    specs = synth.batch_specs(24, seed=31, side_hi=768, gen_lo=3, gen_hi=40)
+    cells = [synth.bernoulli_board(s.rows, s.cols, s.density, s.seed) for s in specs]
+    words = [synth.pack_cells(c) for c in cells]
+    flat = np.concatenate([w.reshape(-1) for w in words])
+    pin_in = torch.empty(flat.size, dtype=torch.int64, pin_memory=True)
+    host_in = pin_in.numpy().view(np.uint64)
+    host_in[:] = flat
+    sets = [[gol.Board(s.rows, s.cols) for s in specs] for _ in range(2)]
+    handles = [np.array([b.handle for b in bs], dtype=np.uint64) for bs in sets]
+    outs = [torch.empty(flat.size, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64) for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    gens = np.array([s.gens for s in specs], dtype=np.int64)
+    want = np.concatenate([synth.pack_cells(oracle.run(c, s.gens)).reshape(-1) for c, s in zip(cells, specs)])
+    try:
+        events = [None, None]
+        for i in range(6):
+            k = i % 2
+            if events[k] is not None:
+                events[k].synchronize()
+                assert np.array_equal(outs[k], want), "set %d after step %d" % (k, i - 2)
+                outs[k][:] = 0
+            gol.gol_set_stream(streams[k])
+            gol.gol_set_packed_batch(handles[k], host_in)
+            gol.gol_step_batch(handles[k], gens)
+            gol.gol_get_packed_batch_async(handles[k], outs[k])
+            events[k] = torch.cuda.Event()
+            events[k].record(streams[k])
+        for k in range(2):
+            events[k].synchronize()
+            assert np.array_equal(outs[k], want), "set %d at the end" % k
+    finally:
+        gol.gol_set_stream(None)
+        for bs in sets:
+            for b in bs:
+                b.close()
+        gol.gol_set_allocator(None, None)
