@@ -20,6 +20,11 @@
  *     message for the calling thread is available from gol_last_error();
  *   - stepping is asynchronous on the library's current CUDA stream
  *     (gol_set_stream); calls that return data to the host synchronise it.
+ *     The tables a launch needs (unit plans, transfer plans) are copied to
+ *     the device from page-locked staging blocks that the library keeps
+ *     for the life of the process (at most 32, each reused once the copy
+ *     from it has run), so queuing a launch does not wait for the work
+ *     already on the stream.
  *
  * The library needs a CUDA GPU; there is no CPU path.  Calls made without
  * one return GOL_ECUDA.

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -145,6 +146,103 @@ void dev_free(void *p, void (*ff)(void *, void *), void *ctx) {
 }
 
 void defer_free(void *p, void (*ff)(void *, void *), void *ctx);
+
+// ---------------------------------------------------------------------------
+// page-locked staging of table uploads
+// ---------------------------------------------------------------------------
+// A launch uploads tables built on the host (a unit plan, a transfer plan).
+// A cudaMemcpyAsync from pageable memory may wait for the work already
+// queued on the stream before it copies, which would hold the caller until
+// the previous launch has finished; a copy from page-locked memory is only
+// queued.  Staging blocks are kept for reuse (page-locked allocation is
+// slow; they live as long as the process) and handed out again once an
+// event recorded behind their last copy has completed.
+struct StageBlock {
+    char *p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+};
+std::vector<StageBlock> &g_stage = *new std::vector<StageBlock>();
+constexpr size_t kStageBlocks = 32;                  // a launch and a transfer plan per tick, a few ticks ahead
+constexpr size_t kStageMin = size_t(256) << 10;
+
+struct Upload {
+    void *dst;           // device
+    const void *src;     // host
+    size_t n;            // bytes
+};
+
+// A free staging block of at least `total` bytes, or null (none free and no
+// room for another).
+StageBlock *stage_block(size_t total) {
+    StageBlock *b = nullptr;
+    for (auto &s : g_stage) {
+        if (s.cap < total) continue;
+        if (s.pending) {
+            if (cudaEventQuery(s.ev) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            s.pending = false;
+        }
+        if (!b || s.cap < b->cap) b = &s;
+    }
+    if (b || g_stage.size() >= kStageBlocks) return b;
+    StageBlock s;
+    s.cap = kStageMin;
+    while (s.cap < total) s.cap *= 2;
+    if (cudaHostAlloc((void **)&s.p, s.cap, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(s.p);
+        return nullptr;
+    }
+    g_stage.push_back(s);
+    return &g_stage.back();
+}
+
+// Queues the copies `parts` on the library's stream through one staging
+// block (each part at a 16-byte offset).  While the stream is being
+// captured, or when no block is free, the parts are copied from where they
+// are.
+cudaError_t upload(std::initializer_list<Upload> parts) {
+    size_t total = 0;
+    for (const Upload &u : parts) total += (u.n + 15) & ~size_t(15);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
+    if (cudaStreamIsCapturing(g_stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;
+    }
+    StageBlock *b = (cs == cudaStreamCaptureStatusNone && total > 0) ? stage_block(total) : nullptr;
+    size_t off = 0;
+    for (const Upload &u : parts) {
+        if (u.n == 0) continue;
+        const void *src = u.src;
+        if (b) {
+            std::memcpy(b->p + off, u.src, u.n);
+            src = b->p + off;
+            off += (u.n + 15) & ~size_t(15);
+        }
+        cudaError_t e = cudaMemcpyAsync(u.dst, src, u.n, cudaMemcpyHostToDevice, g_stream);
+        if (e != cudaSuccess) {
+            if (b) cudaStreamSynchronize(g_stream);   // copies already queued from the block have run
+            return e;
+        }
+    }
+    if (b) {
+        cudaError_t e = cudaEventRecord(b->ev, g_stream);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(g_stream);
+            return e;
+        }
+        b->pending = true;
+    }
+    return cudaSuccess;
+}
 
 // scoped temporary device buffer using the process allocator.  With an
 // allocator hook the buffer is returned once the work queued on the stream
@@ -584,10 +682,9 @@ int build_plan(Plan &P) {
     P.alloc_ctx = g_alloc_ctx;
     if (!P.dmem) return fail(GOL_ENOMEM, "plan workspace of %zu bytes", P.dbytes);
     char *base = (char *)P.dmem;
-    CU(cudaMemcpyAsync(base, P.boards.data(), nb * sizeof(BoardDesc), cudaMemcpyHostToDevice, g_stream));
-    CU(cudaMemcpyAsync(base + o_units, P.units.data(), nu * sizeof(UnitDesc), cudaMemcpyHostToDevice,
-                       g_stream));
-    CU(cudaMemcpyAsync(base + o_init, P.init_order.data(), nu * 4, cudaMemcpyHostToDevice, g_stream));
+    CU(upload({{base, P.boards.data(), nb * sizeof(BoardDesc)},
+                {base + o_units, P.units.data(), nu * sizeof(UnitDesc)},
+                {base + o_init, P.init_order.data(), nu * 4}}));
     a.boards = (const BoardDesc *)base;
     a.units = (const UnitDesc *)(base + o_units);
     a.run = (UnitRun *)(base + o_run);
@@ -1230,8 +1327,7 @@ int copy_plan(const gol_handle *hs, size_t n, const CopyPlan **out) {
     P->alloc_ctx = g_alloc_ctx;
     P->dmem = dev_alloc(P->board_off + bb.size() * 4 + 4, g_alloc, g_alloc_ctx);
     if (!P->dmem) return fail(GOL_ENOMEM, "transfer plan of %zu boards", n);
-    CU(cudaMemcpyAsync(P->dmem, d.data(), n * sizeof(CopyDesc), cudaMemcpyHostToDevice, g_stream));
-    CU(cudaMemcpyAsync((char *)P->dmem + P->board_off, bb.data(), bb.size() * 4, cudaMemcpyHostToDevice, g_stream));
+    CU(upload({{P->dmem, d.data(), n * sizeof(CopyDesc)}, {(char *)P->dmem + P->board_off, bb.data(), bb.size() * 4}}));
     g_copy_plans.insert(g_copy_plans.begin(), std::move(P));
     if (g_copy_plans.size() > kMaxCopyPlans) g_copy_plans.pop_back();
     *out = g_copy_plans[0].get();

@@ -5,12 +5,15 @@ The server keeps every admitted board resident on the device, admits waiting
 requests in arrival order while their two device buffers fit the memory
 budget, and advances all admitted boards together, one ``gol_step_batch``
 launch per tick.  Each tick gives every active board a quantum of
-generations (at most what it still needs); the quantum adapts so that a tick
-lasts about ``tick_target_s`` of device time (10 ms: on the bench's stream
-ticks of 10 to 80 ms give the same throughput within 2 %, and the shortest
-halve the median latency).  The stepping itself is the
-library's persistent launch, so the result of every request is
-bit-identical to stepping it alone.
+generations (at most what it still needs), sized so that a tick lasts about
+``tick_target_s`` of device time (10 ms: on the bench's stream ticks of 10
+to 80 ms give the same throughput within 2 %, and the shortest halve the
+median latency).  Every board of a tick gets the same quantum, so their
+chains of passes are about equally long and the launch stays dense (giving
+small boards more generations, up to what their chain covers in a tick,
+made the ticks chain-bound: 46 - 69 % of the rate on the bench's stream).
+The stepping itself is the library's persistent launch, so the result of
+every request is bit-identical to stepping it alone.
 
 The loop never waits for the device while there is something to queue:
 ticks are launched ahead (up to ``depth`` in flight on the library's
@@ -20,10 +23,12 @@ result copy is queued right behind that tick and the next tick, without
 those boards, is queued right after.  An event recorded behind each tick
 tells the host when the tick, and the copies of the boards it finished, are
 done; only then are those requests answered, their boards destroyed and
-their memory returned to the budget.  Arrivals are admitted (created, and
-their cells uploaded from page-locked memory) between launches, so their
-uploads queue behind the ticks already in flight and they join the next
-tick launched.
+their memory returned to the budget.  Arrivals are admitted between
+launches, all those admitted at once as one group (created, their cells
+copied into one page-locked buffer that one many-board upload reads in
+place), on a side stream, so that the admission runs while the ticks in
+flight compute; the next tick launched waits for it and takes the new
+boards in.
 
 ``serve_fcfs`` is the baseline that serves the same trace one request at a
 time with ``gol_step``.
@@ -31,6 +36,7 @@ time with ``gol_step``.
 from __future__ import annotations
 
 import collections
+import contextlib
 import time
 from dataclasses import dataclass, field
 from typing import Callable, Sequence
@@ -95,30 +101,61 @@ class ServeStats:
 
 class GpuBackend:
     """The library on the GPU plus the stream plumbing the loop needs:
-    events and copies on the library's stream (PyTorch's current stream,
-    which ``gol.use_torch_allocator`` makes the library's), page-locked
-    staging of uploads and asynchronous result copies."""
+    ticks, events and result copies on the library's stream (PyTorch's
+    current stream, which ``gol.use_torch_allocator`` makes the library's),
+    admissions on a side stream, page-locked staging of uploads and
+    asynchronous result copies."""
 
     def __init__(self):
         import torch
 
         self.torch = torch
         self.stream = torch.cuda.current_stream()
-        gol.gol_set_stream(self.stream)     # library work, events and copies on one stream
+        self.side = torch.cuda.Stream()
+        gol.gol_set_stream(self.stream)     # ticks, events and result copies on one stream
+
+    def start(self):
+        """Before serving: the side stream waits for the work queued so far."""
+        self.side.wait_stream(self.stream)
+
+    @contextlib.contextmanager
+    def admission(self):
+        """Library calls made inside run on the side stream: the creation
+        and upload of new boards overlap the ticks in flight, and the
+        library's stream waits for them before its next launch.  The two
+        streams share nothing in flight: new boards belong to no queued
+        tick, and device memory goes back to the allocator only when idle
+        (the library frees boards, plans and staging buffers after an event
+        recorded behind their last use; result buffers are kept until their
+        tick has completed)."""
+        gol.gol_set_stream(self.side)
+        try:
+            yield
+        finally:
+            ev = self.torch.cuda.Event()
+            ev.record(self.side)
+            gol.gol_set_stream(self.stream)
+            self.stream.wait_event(ev)
 
     def gol_create_ex(self, rows, cols, torus, layout):
         return gol.gol_create_ex(rows, cols, torus, layout)
 
-    def stage(self, words: np.ndarray):
-        """Page-locked copy of a request's cells (the upload then runs
-        asynchronously on the stream)."""
-        t = self.torch.empty(words.size, dtype=self.torch.int64, pin_memory=True)
-        v = t.numpy().view(np.uint64)
-        v[:] = words.reshape(-1)
-        return t, v.reshape(words.shape)
-
     def gol_set_packed(self, h, words):
         gol.gol_set_packed(h, words)
+
+    def upload_group(self, hs, words_list):
+        """Uploads the cells of several new boards with one many-board
+        transfer that reads one page-locked buffer in place; returns that
+        buffer (to be kept until the upload has run)."""
+        n = sum(w.size for w in words_list)
+        t = self.torch.empty(n, dtype=self.torch.int64, pin_memory=True)
+        flat = t.numpy().view(np.uint64)
+        off = 0
+        for w in words_list:
+            flat[off:off + w.size] = w.reshape(-1)
+            off += w.size
+        gol.gol_set_packed_batch(hs, flat)
+        return t
 
     def gol_step_batch(self, hs, gens):
         gol.gol_step_batch(hs, gens)
@@ -136,7 +173,7 @@ class GpuBackend:
         gol.gol_get_packed_device(h, dev.data_ptr(), n)
         host = torch.empty(n, dtype=torch.int64, pin_memory=True)
         host.copy_(dev, non_blocking=True)
-        return _Pending(host, rows, cols // 64)
+        return _Pending(host, rows, cols // 64, dev)
 
     def record(self):
         ev = self.torch.cuda.Event(enable_timing=True)
@@ -154,8 +191,10 @@ class GpuBackend:
 
 
 class _Pending:
-    def __init__(self, host, rows, words):
-        self.host, self.shape = host, (rows, words)
+    def __init__(self, host, rows, words, dev=None):
+        # the device buffer stays allocated until the copy has run (freed
+        # earlier, the allocator could hand it to an upload on the side stream)
+        self.host, self.shape, self.dev = host, (rows, words), dev
 
     def result(self) -> np.ndarray:
         return self.host.numpy().view(np.uint64).reshape(self.shape).copy()
@@ -187,14 +226,23 @@ class Server:
         self.rate_cups = None             # measured cell updates per second of device time
         self._per_gen = 0                 # cells of the boards in the last tick
 
-    def _admit(self, job: Job, now: float):
-        job.handle = self.g.gol_create_ex(job.rows, job.cols, True, gol.GOL_LAYOUT_PACKED)
-        words = job.words
-        if hasattr(self.g, "stage"):
-            job.staged, words = self.g.stage(job.words)
-        self.g.gol_set_packed(job.handle, words)
-        job.remaining = job.gens
-        job.admitted_s = now
+    def _admit(self, group: list, now: float):
+        """Creates the boards of the requests in `group` and queues the upload
+        of their cells (one many-board upload when the backend has one, on
+        its admission stream when it has one)."""
+        ctx = self.g.admission() if hasattr(self.g, "admission") else contextlib.nullcontext()
+        with ctx:
+            for job in group:
+                job.handle = self.g.gol_create_ex(job.rows, job.cols, True, gol.GOL_LAYOUT_PACKED)
+                job.remaining = job.gens
+                job.admitted_s = now
+            if hasattr(self.g, "upload_group"):
+                staged = self.g.upload_group([j.handle for j in group], [j.words for j in group])
+                for job in group:
+                    job.staged = staged
+                return
+            for job in group:
+                self.g.gol_set_packed(job.handle, job.words)
 
     def _retire(self, job: Job, now: float, stats: ServeStats):
         if job.pending is not None:
@@ -226,6 +274,8 @@ class Server:
 
     def _run(self, jobs: Sequence[Job], live: list) -> ServeStats:
         jobs = sorted(jobs, key=lambda j: j.arrival_s)
+        if hasattr(self.g, "start"):
+            self.g.start()
         stats = ServeStats()
         waiting: collections.deque = collections.deque()
         inflight: collections.deque = collections.deque()
@@ -247,12 +297,15 @@ class Server:
             while nxt < len(jobs) and jobs[nxt].arrival_s <= now:
                 waiting.append(jobs[nxt])
                 nxt += 1
+            group = []
             while waiting and used + waiting[0].bytes_on_device <= self.budget:
                 j = waiting.popleft()
                 live.append(j)
-                self._admit(j, now)
-                active.append(j)
+                group.append(j)
                 used += j.bytes_on_device
+            if group:
+                self._admit(group, now)
+                active.extend(group)
             if waiting and not live:
                 raise RuntimeError("request %d needs %d bytes, more than the budget" %
                                    (waiting[0].rid, waiting[0].bytes_on_device))
@@ -270,10 +323,16 @@ class Server:
         stats.makespan_s = self.clock() - t0
         return stats
 
+    def _quanta(self, active: list) -> list:
+        """Generations of each active board in the next tick: the quantum,
+        at most what the board still needs."""
+        return [min(j.remaining, self.quantum) for j in active]
+
     def _launch(self, active: list, inflight: collections.deque, stats: ServeStats):
-        """One tick: every active board advances by min(remaining, quantum);
-        boards that reach their count have their result copy queued behind it."""
-        q = [min(j.remaining, self.quantum) for j in active]
+        """One tick: every active board advances by its quantum (at most what
+        it still needs); boards that reach their count have their result
+        copy queued behind it."""
+        q = self._quanta(active)
         cells_gens = sum(j.rows * j.cols * g for j, g in zip(active, q))
         self._per_gen = sum(j.rows * j.cols for j in active)
         start = self.g.record()

@@ -39,6 +39,13 @@ class FakeBackend:
     def gol_set_packed(self, h, words):
         assert words.shape == (self.boards[h]["rows"], self.boards[h]["cols"] // 64)
 
+    def upload_group(self, hs, words_list):
+        assert len(hs) == len(words_list) and len(set(hs)) == len(hs)
+        self.groups = getattr(self, "groups", 0) + 1
+        for h, w in zip(hs, words_list):
+            self.gol_set_packed(h, w)
+        return object()
+
     def gol_step_batch(self, hs, gens):
         assert len(set(hs)) == len(hs)
         self.batches.append(list(zip(hs, gens)))
@@ -90,6 +97,14 @@ def test_host_logic_budget_fifo_and_generations(serve_mod):
     admitted = sorted(jobs, key=lambda j: j.admitted_s)
     assert [j.rid for j in admitted] == sorted(j.rid for j in jobs)   # FIFO admission
     assert st.max_waiting > 0 and st.ticks > 1
+
+
+def test_host_logic_admits_arrivals_in_groups(serve_mod):
+    # requests that arrive together are created and uploaded as one group
+    fake = FakeBackend()
+    jobs = make_jobs(serve_mod, 30, rate=1e6)
+    st = serve_mod.Server(budget_bytes=1 << 40, tick_target_s=1e-4, backend=fake).run(jobs)
+    assert st.summary()["requests"] == 30 and fake.groups < 30 and not fake.boards
 
 
 def test_host_logic_rejects_oversized_request(serve_mod):
