@@ -802,8 +802,9 @@ __device__ __forceinline__ void enqueue(const PersistArgs &A, int v, int64_t rem
 // passes: a ticket is a promise to run what lands in its slot.  The warp
 // takes a critical ticket when the critical ring shows queued passes (one
 // load of its head and tail; the ticket may land past them and then waits
-// for the next critical pass), otherwise an other-ring ticket, and serves
-// whichever slot fills first, the critical one when both have.  Returns the
+// for the next critical pass, alone for up to kCriticalWaitNs), otherwise an
+// other-ring ticket, and serves whichever slot fills first, the critical one
+// when both have.  Returns the
 // unit (its pass is in next_pass), or -1 when every pass of the launch has
 // completed or the launch failed.  Bounded: no completed pass for
 // timeout_ns sets GOL_ETIMEOUT.
@@ -826,21 +827,43 @@ __device__ __forceinline__ int ticket_unit(const PersistArgs &A, int (&tk)[2]) {
     return -1;
 }
 
-static __device__ int take_work(const PersistArgs &A, int (&tk)[2]) {
+// A critical ticket taken when the critical ring showed queued passes may
+// land past them (other warps took those first).  Its holder waits up to
+// kCriticalWaitNs for the next critical pass before it takes or serves
+// other-ring work: a critical pass that lands in the slot of a warp busy
+// with an other-ring pass waits for that pass to end (on the 4096-board
+// batch the wait gains about 1 % of the makespan; windows of 20 to 200 us
+// measure the same).  The wait is bounded: an endless one could leave every
+// warp waiting for critical passes that are never queued.
+constexpr uint64_t kCriticalWaitNs = 20000;
+
+static __device__ int take_work(const PersistArgs &A, int (&tk)[2], uint32_t &tk0_ns) {
     uint64_t t_last = global_ns();
     int seen = -1;
     unsigned ns = 32;
     for (long long spin = 0; spin < (1ll << 32); ++spin) {
-        const int v = ticket_unit(A, tk);
-        if (v >= 0) return v;
+        // low 32 bits of the timer: the difference is exact for windows below 4 s
+        const bool crit_wait = tk[0] >= 0 && tk[0] < A.hi_cap &&
+                               (uint32_t)global_ns() - tk0_ns < (uint32_t)kCriticalWaitNs;
+        if (crit_wait) {
+            const int v = ld_acquire(&A.ring[tk[0]]);
+            if (v >= 0) {
+                tk[0] = -1;
+                return v;
+            }
+        } else {
+            const int v = ticket_unit(A, tk);
+            if (v >= 0) return v;
+        }
         if (tk[0] < 0 && A.hi_cap > 0 && (spin & 7) == 0) {
             const int2 ht = ld_relaxed_v2(&A.qctr[0]);
             if (ht.x < ht.y) {
                 tk[0] = atomicAdd(&A.qctr[0], 1);
+                tk0_ns = (uint32_t)global_ns();
                 continue;
             }
         }
-        if (tk[1] < 0) {
+        if (tk[1] < 0 && !crit_wait) {
             tk[1] = atomicAdd(&A.qctr[2], 1);
             continue;
         }
@@ -954,12 +977,22 @@ persistent_step_kernel(const PersistArgs A) {
     const int w = blockIdx.x * kWarpsPerBlock + (int)(threadIdx.x >> 5);
     // warp w < hi_init starts with the critical ring's slot w (pass 1)
     int u = w < min(A.hi_init, A.nwarps) ? A.ring[w] : -1, pass = 1;
-    int tk[2] = {-1, -1};    // lane 0: the tickets this warp holds (critical, other)
+    // lane 0's scheduling state, in shared memory (used between passes only,
+    // it stays out of the registers of the pass): the tickets this warp holds
+    // (critical, other) and when it took its critical ticket
+    __shared__ int s_tk[kWarpsPerBlock][2];
+    __shared__ uint32_t s_tk0[kWarpsPerBlock];
+    int (&tk)[2] = s_tk[threadIdx.x >> 5];
+    uint32_t &tk0_ns = s_tk0[threadIdx.x >> 5];
+    if (lane == 0) {
+        tk[0] = tk[1] = -1;
+        tk0_ns = 0;
+    }
     for (;;) {
         if (u < 0) {
             int v = -1, p = 0;
             if (lane == 0) {
-                v = take_work(A, tk);
+                v = take_work(A, tk, tk0_ns);
                 // written before the slot by the thread that queued v; the
                 // slot's acquire load orders this read after it
                 if (v >= 0) p = A.next_pass[v];

@@ -9,9 +9,12 @@ parity that a unit restores when it starts its next pass, two queue rings
 (critical passes, whose unit still has at least a given share of the longest
 chain ahead, and the others) whose slots are handed out only by atomic
 tickets, a warp holding at most one ticket of each ring until its slot
-fills, and the first critical passes dealt to warps by index.  Every run
-must execute every pass exactly once, never start a pass before its
-neighbours finished the previous one, never overflow a ring, and end.
+fills, a warp whose critical ticket is still unfilled waiting for it alone
+for a bounded time (counted here in the warp's own steps) before it takes or
+serves other-ring work, and the first critical passes dealt to warps by
+index.  Every run must execute every pass exactly once, never start a pass
+before its neighbours finished the previous one, never overflow a ring, and
+end.
 """
 import random
 
@@ -55,7 +58,9 @@ def plan_rings(units, npass, permille):
     return thr, hi_cap, hi_init, order
 
 
-def run(units, npass, nwarps, permille, seed):
+def run(units, npass, nwarps, permille, seed, crit_wait=0):
+    """crit_wait: how many of its own steps a warp holding an unfilled
+    critical ticket waits for it alone (INF: without limit)."""
     rng = random.Random(seed)
     n = len(units)
     thr, hi_cap, hi_init, order = plan_rings(units, npass, permille)
@@ -98,11 +103,19 @@ def run(units, npass, nwarps, permille, seed):
     def warp(w):
         u = ring[w] if w < min(hi_init, nwarps) else -1
         p, tk = 1, [-1, -1]
+        clock = {"now": 0, "tk0": 0}          # the warp's own steps; when it took tk[0]
         while True:
             if u < 0:
                 spin = 0
                 while True:
-                    v = ticket_unit(tk)
+                    clock["now"] += 1
+                    waiting = 0 <= tk[0] < hi_cap and clock["now"] - clock["tk0"] < crit_wait
+                    if waiting:
+                        v = ring[tk[0]]
+                        if v >= 0:
+                            tk[0] = -1
+                    else:
+                        v = ticket_unit(tk)
                     if v >= 0:
                         break
                     if tk[0] < 0 and hi_cap > 0 and spin % 8 == 0:
@@ -111,10 +124,11 @@ def run(units, npass, nwarps, permille, seed):
                         if head < tail:
                             tk[0] = q[0]
                             q[0] += 1
+                            clock["tk0"] = clock["now"]
                             yield
                             spin += 1
                             continue
-                    if tk[1] < 0:
+                    if tk[1] < 0 and not waiting:
                         tk[1] = q[2]
                         q[2] += 1
                         yield
@@ -127,6 +141,7 @@ def run(units, npass, nwarps, permille, seed):
                 u, p = v, next_pass[v]
                 yield
             # run pass p of u
+            clock["now"] += 1
             assert (u, p) not in ran, "a pass ran twice"
             for x in units[u]["nb"]:
                 assert finished.get(x, 0) >= p - 1, "a pass started before a neighbour's previous pass"
@@ -172,7 +187,8 @@ def run(units, npass, nwarps, permille, seed):
     steps = 0
     while live:
         steps += 1
-        assert steps < 3_000_000, "no progress (deadlock or livelock)"
+        if steps >= 3_000_000:
+            raise RuntimeError("no progress (deadlock or livelock)")
         i = rng.randrange(len(live))
         try:
             next(gens[live[i]])
@@ -189,6 +205,32 @@ def test_two_ring_ticket_protocol(permille):
         boards = [(r.randint(1, 4), r.randint(1, 3), r.randint(1, 20)) for _ in range(nboards)]
         npass = [r.randint(1, 9) for _ in range(nboards)]
         run(make_units(boards), npass, r.randint(2, 10), permille, seed)
+
+
+@pytest.mark.parametrize("crit_wait", [1, 6, 40])
+def test_bounded_wait_for_a_critical_ticket(crit_wait):
+    for seed in range(120):
+        r = random.Random(7000 + 100 * crit_wait + seed)
+        nboards = r.randint(1, 6)
+        boards = [(r.randint(1, 4), r.randint(1, 3), r.randint(1, 20)) for _ in range(nboards)]
+        npass = [r.randint(1, 9) for _ in range(nboards)]
+        run(make_units(boards), npass, r.randint(2, 10), r.choice([250, 500, 750]), seed, crit_wait)
+
+
+def test_unbounded_wait_for_a_critical_ticket_can_stall():
+    # why the kernel's wait has a time limit: warps holding critical tickets
+    # that no queued pass will fill, waiting without limit, leave the queued
+    # other-ring passes to nobody
+    stalled = 0
+    for seed in range(60):
+        r = random.Random(9000 + seed)
+        boards = [(r.randint(2, 4), r.randint(1, 3), r.randint(1, 20)) for _ in range(r.randint(2, 6))]
+        npass = [r.randint(2, 9) for _ in range(len(boards))]
+        try:
+            run(make_units(boards), npass, r.randint(2, 6), 500, seed, INF)
+        except RuntimeError:
+            stalled += 1
+    assert stalled > 0
 
 
 def test_join_counters_two_parities_suffice():
