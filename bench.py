@@ -799,7 +799,53 @@ def run_decomposition(args):
                                  "gcups": round(R * C * iters / dt / 1e9, 5)})
     print(json.dumps({"metric": "host decomposition study (paper Table 2 shapes)", "cores": nproc,
                       "data": "synthetic Bernoulli(0.3) boards; the paper's figure-3 pattern is not in the text",
-                      "rows": rows}), flush=True)
+                      "rows": rows, "gpu": gpu_decomposition(((60, 120), (120, 240)), (500, 1000, 2000))}),
+          flush=True)
+
+
+def gpu_decomposition(shapes, iterations):
+    """Beside the host study: the GPU library's own decomposition of the same
+    boards (the autotuner's generations per pass and tile rows for their size
+    class, and the unit plan they give: row blocks x word tiles, segments per
+    warp), and, when a GPU is present, the same boards stepped on it in the
+    default layout and in the packed one (GCUPS over the table's iteration
+    counts, CUDA events)."""
+    from paper_1209_4408_gb300 import gol
+
+    out = []
+    for (R, C) in shapes:
+        W = (C + 63) // 64
+        k, tr = gol.gol_tune_get(R, C)
+        units = gol.gol_plan_units(R, W, k, tr)
+        u0 = units[0]
+        entry = {"board": "%dx%d" % (R, C), "gens_per_pass": k, "tile_rows": tr, "units": len(units),
+                 "plan": ("%d row block(s) of full rows, %d segment(s) of %d rows per warp" % (len(units), u0["S"], u0["H"])
+                          if u0["mode"] == 0 else "%d row block(s) x word tiles" % len(units))}
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                cells = synth.bernoulli_board(R, C, 0.3, 14408)
+                for name, layout in (("default", gol.GOL_LAYOUT_AUTO), ("packed", gol.GOL_LAYOUT_PACKED)):
+                    b = gol.Board(R, C, layout=layout)
+                    b.set(cells)
+                    b.step(iterations[0])
+                    b.sync()
+                    res = {"layout": "bytes" if b.layout == gol.GOL_LAYOUT_BYTES else "packed"}
+                    for it in iterations:
+                        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        ev0.record()
+                        b.step(it)
+                        ev1.record()
+                        b.sync()
+                        ms = ev0.elapsed_time(ev1)
+                        res["gcups_%d" % it] = round(R * C * it / (ms * 1e-3) / 1e9, 3)
+                    entry[name] = res
+                    b.close()
+        except ImportError:
+            pass
+        out.append(entry)
+    return out
 
 
 def run_reference(args, rank, world):
