@@ -829,10 +829,10 @@ def gpu_decomposition(shapes, iterations):
                 for name, layout in (("default", gol.GOL_LAYOUT_AUTO), ("packed", gol.GOL_LAYOUT_PACKED)):
                     b = gol.Board(R, C, layout=layout)
                     b.set(cells)
-                    b.step(iterations[0])
-                    b.sync()
                     res = {"layout": "bytes" if b.layout == gol.GOL_LAYOUT_BYTES else "packed"}
                     for it in iterations:
+                        b.step(it)                  # warm-up: the plan (or graph) of this count
+                        b.sync()
                         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                         ev0.record()
                         b.step(it)
