@@ -30,6 +30,13 @@ place), on a side stream, so that the admission runs while the ticks in
 flight compute; the next tick launched waits for it and takes the new
 boards in.
 
+When the input is closed (every request of the trace has arrived and none
+waits for memory), the boards still active get all their remaining
+generations in one last launch (``drain``): nothing can join a later tick,
+and one launch lets the library's planner split the long runs that are left
+into as many units as the device has warps, instead of stepping them tick
+by tick behind the largest board.
+
 ``serve_fcfs`` is the baseline that serves the same trace one request at a
 time with ``gol_step``.
 """
@@ -212,7 +219,7 @@ class Server:
     def __init__(self, budget_bytes: int = 120 << 30, tick_target_s: float = 0.01,
                  quantum_min: int = 8, quantum_max: int = 1 << 16, keep_results: bool = False,
                  clock: Callable[[], float] = time.perf_counter, backend=None, depth: int = 2,
-                 sleep: Callable[[float], None] = time.sleep, poll_s: float = 2e-4):
+                 sleep: Callable[[float], None] = time.sleep, poll_s: float = 2e-4, drain: bool = True):
         self.g = backend if backend is not None else GpuBackend()
         self.budget = budget_bytes
         self.tick_target = tick_target_s
@@ -222,6 +229,7 @@ class Server:
         self.depth = max(1, depth)
         self.sleep = sleep
         self.poll = poll_s
+        self.drain = drain
         self.quantum = quantum_min
         self.rate_cups = None             # measured cell updates per second of device time
         self._per_gen = 0                 # cells of the boards in the last tick
@@ -313,7 +321,8 @@ class Server:
             stats.max_active = max(stats.max_active, len(active))
             stats.peak_bytes = max(stats.peak_bytes, used)
             if active and len(inflight) < self.depth:
-                self._launch(active, inflight, stats)
+                closed = self.drain and nxt >= len(jobs) and not waiting
+                self._launch(active, inflight, stats, closed)
                 continue
             if not inflight and not active and nxt < len(jobs):
                 # idle until the next arrival
@@ -323,16 +332,19 @@ class Server:
         stats.makespan_s = self.clock() - t0
         return stats
 
-    def _quanta(self, active: list) -> list:
+    def _quanta(self, active: list, closed: bool = False) -> list:
         """Generations of each active board in the next tick: the quantum,
-        at most what the board still needs."""
+        at most what the board still needs; all it needs once the input is
+        closed."""
+        if closed:
+            return [j.remaining for j in active]
         return [min(j.remaining, self.quantum) for j in active]
 
-    def _launch(self, active: list, inflight: collections.deque, stats: ServeStats):
+    def _launch(self, active: list, inflight: collections.deque, stats: ServeStats, closed: bool = False):
         """One tick: every active board advances by its quantum (at most what
         it still needs); boards that reach their count have their result
         copy queued behind it."""
-        q = self._quanta(active)
+        q = self._quanta(active, closed)
         cells_gens = sum(j.rows * j.cols * g for j, g in zip(active, q))
         self._per_gen = sum(j.rows * j.cols for j in active)
         start = self.g.record()

@@ -107,6 +107,31 @@ def test_host_logic_admits_arrivals_in_groups(serve_mod):
     assert st.summary()["requests"] == 30 and fake.groups < 30 and not fake.boards
 
 
+def test_host_logic_drains_in_one_launch_once_input_is_closed(serve_mod):
+    # once every request has arrived (and none waits for memory) the active
+    # boards get all their remaining generations in one launch; before, the
+    # quantum; with drain=False the quantum to the end
+    clock = TickClock()
+    jobs = make_jobs(serve_mod, 20, rate=2000.0, gen_hi=3000)
+    fake = ClockedBackend(clock, jobs)
+    srv = serve_mod.Server(budget_bytes=1 << 40, tick_target_s=5e-3, quantum_min=8, keep_results=True,
+                           clock=clock, backend=fake, sleep=clock.sleep)
+    srv.run(jobs)
+    assert all(j.result == j.gens for j in jobs) and not fake.boards
+    final = fake.batches[-1]
+    assert len(final) > 1                                   # several boards finished together
+    # the last launch gave boards more generations than any earlier tick's quantum
+    assert max(g for _, g in final) > max(g for b in fake.batches[:-1] for _, g in b)
+    clock2 = TickClock()
+    jobs2 = make_jobs(serve_mod, 20, rate=2000.0, gen_hi=3000)
+    fake2 = ClockedBackend(clock2, jobs2)
+    srv2 = serve_mod.Server(budget_bytes=1 << 40, tick_target_s=5e-3, quantum_min=8, keep_results=True,
+                            clock=clock2, backend=fake2, sleep=clock2.sleep, drain=False)
+    srv2.run(jobs2)
+    assert all(j.result == j.gens for j in jobs2)
+    assert len(fake2.batches) > len(fake.batches)
+
+
 def test_host_logic_rejects_oversized_request(serve_mod):
     fake = FakeBackend()
     jobs = make_jobs(serve_mod, 3, rate=1e6)
@@ -132,7 +157,7 @@ class FailingBackend(FakeBackend):
 def test_host_logic_frees_boards_when_a_step_fails(serve_mod, fail_at):
     fake = FailingBackend(fail_at)
     jobs = make_jobs(serve_mod, 12, rate=1e6, gen_hi=200)
-    srv = serve_mod.Server(budget_bytes=1 << 30, tick_target_s=1e-4, backend=fake)
+    srv = serve_mod.Server(budget_bytes=1 << 30, tick_target_s=1e-4, backend=fake, drain=False)
     with pytest.raises(RuntimeError, match="step failed"):
         srv.run(jobs)
     assert not fake.boards and fake.live_bytes == 0
