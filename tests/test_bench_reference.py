@@ -43,3 +43,20 @@ def test_reference_line(workload):
 
 def test_reference_other_ranks_exit_quietly():
     assert run_reference("batch", {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_gpu_decomposition_plan_without_gpu():
+    # beside the host decomposition study, the GPU library's own choice for
+    # the Table 2 shapes comes from the host-side planner alone: the tuned
+    # generations per pass and tile rows, and a unit plan that covers the
+    # board (rows of the segments of all units add up to the board's rows)
+    import bench
+    from paper_1209_4408_gb300 import gol
+
+    out = bench.gpu_decomposition(((60, 120), (120, 240)), (500,))
+    assert [e["board"] for e in out] == ["60x120", "120x240"]
+    for e, (R, C) in zip(out, ((60, 120), (120, 240))):
+        assert (e["gens_per_pass"], e["tile_rows"]) == gol.gol_tune_get(R, C)
+        units = gol.gol_plan_units(R, (C + 63) // 64, e["gens_per_pass"], e["tile_rows"])
+        assert e["units"] == len(units)
+        assert sum(u["r_end"] - u["r0"] for u in units if u["mode"] == 0) == R
